@@ -1,0 +1,165 @@
+/*
+ * lindblad.h -- C ABI of the B300 (sm_103a) Lindblad steady-state / low-spectrum library.
+ *
+ * Method: Beugnot, Gregory, Robin, Tilloy, "Well-conditioned iterative methods for large
+ * open quantum systems".  The Lindbladian L = S + K is split into the no-jump part
+ * S(X) = G X + X G^dag, G = -iH - 1/2 sum_j L_j^dag L_j, and the jump part
+ * K(X) = sum_j L_j X L_j^dag (Eqs. (2)-(3)).  S is inverted exactly by a Lyapunov solve
+ * (App. A.1); Phi = -K S^{-1} is a CPTP map whose fixed point gives the steady state
+ * (Theorem 1, Alg. 4), and the no-jump resolvent R_mu^S = (mu - S)^{-1} preconditions the
+ * shift-invert solves of the low-lying spectrum (Sec. 3.1, Alg. 2, Alg. 5).
+ *
+ * Conventions common to every entry point
+ *   - Matrices are dense complex128 (two doubles: re, im), row-major, C-contiguous,
+ *     leading dimension n.  A stack of d matrices is d*n*n contiguous elements.
+ *   - Every pointer argument named *_dev is a DEVICE pointer owned by the caller.
+ *     The library never frees caller memory and allocates no device memory of its
+ *     own: everything it keeps lives in the caller-provided workspace.
+ *   - `stream` is a cudaStream_t passed as void*.  Calls are stream-ordered.  A call
+ *     that returns solver results (steady_state, low_spectrum) synchronises the
+ *     stream before returning, because its stopping test is read on the host once
+ *     per restart.
+ *   - Return value: lb_status.  Negative = no result; 0 = OK; positive = a usable
+ *     result with a caveat (e.g. LB_NOT_CONVERGED returns the running best).
+ *   - A handle must not be used from two streams at once.
+ */
+#ifndef LINDBLAD_H_
+#define LINDBLAD_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LB_OK = 0,
+    LB_NOT_CONVERGED = 1,      /* tolerance not met within the restart cap; best iterate returned */
+    LB_S_SINGULAR = 2,         /* Theorem 1 case 1: G has an eigenvalue on iR, S is not invertible;
+                                  steady_state returns the pure state |psi><psi| of that eigenvector */
+    LB_ILL_CONDITIONED = 3,    /* eigenbasis route refused by the cond(U) gate; Schur route used */
+    LB_INVALID_ARG = -1,
+    LB_CUDA_ERROR = -2,
+    LB_ETA_EXCLUDED = -3,      /* eta * Tr R_mu^S(I) == 1: the Sherman-Morrison preconditioner of
+                                  Eq. ShermanMorr / Alg. 2 is undefined */
+    LB_WORKSPACE_TOO_SMALL = -4,
+    LB_NOT_IMPLEMENTED = -5,
+    LB_SOLVER_ERROR = -6       /* a factorisation in set-up failed (info != 0) */
+} lb_status;
+
+typedef enum {
+    LB_PREC_FP64 = 0,   /* every contraction in FP64 on the CUDA cores */
+    LB_PREC_MIXED = 1   /* jump-term and Sylvester-update GEMMs on the tensor cores (tcgen05,
+                           BF16 split, FP32 accumulate); FP64 Sylvester leaves, FP64 residual,
+                           FP64 iterative refinement of the steady state */
+} lb_precision;
+
+typedef enum { LB_FORM_PHI = 0, LB_FORM_M = 1 } lb_form;   /* Phi = -K S^{-1}; M = -S^{-1} K */
+
+/* phi_apply flags: form in bit 0; coordinates in bit 1 */
+#define LB_APPLY_FORM_M   1   /* apply M instead of Phi */
+#define LB_APPLY_SCHUR    2   /* X and Y are given in Schur coordinates X~ = Q^dag X Q */
+
+typedef struct {
+    double tol;           /* stop when ||L(rho_hat)||_max < tol (absolute, hermitised trace-1 state);
+                             default 1e-10 */
+    int    krylov_m;      /* Arnoldi cycle length m (default 20) */
+    int    max_restarts;  /* N of Alg. 4 / restart cap of Alg. 5 (default 60) */
+    int    precision;     /* lb_precision (default LB_PREC_FP64) */
+    double eta;           /* deflation coefficient eta (default 1) */
+    int    max_refine;    /* mixed precision: refinement steps cap (default 8) */
+    int    gmres_m;       /* inner GMRES cycle length (default 20) */
+    int    sylv_block;    /* triangular Sylvester block size (default 0 = automatic) */
+    double inner_tol;     /* shift-invert inner GMRES relative tolerance (default 1e-12) */
+    int    keep_ritz;     /* p of Alg. 5: Ritz pairs kept at a thick restart (default 0 = auto) */
+} lb_opts;
+
+typedef struct {
+    int    status;
+    int    restarts;          /* Arnoldi cycles run */
+    int    phi_applies;       /* Phi (or OP) applications */
+    int    gmres_steps;       /* inner GMRES steps (refinement / shift-invert) */
+    int    refine_steps;      /* mixed-precision refinement steps */
+    double residual_max;      /* ||L(rho_hat)||_max of the returned state (FP64, original basis) */
+    double residual_fro;      /* ||L(rho_hat)||_F */
+    double ritz_value;        /* Ritz value of Phi selected at the end (steady_state) */
+    double schur_backward_err;/* ||strictly-lower(Q^dag G Q)||_F / ||G||_F left out of T */
+    double min_abs_re_T;      /* min_i |Re T_ii| (case-1 test of Theorem 1) */
+    double setup_ms;          /* lindblad_setup wall time (host clock around the stream) */
+    double solve_ms;          /* wall time of the call that filled this struct */
+} lb_info;
+
+typedef struct lb_handle_s* lindblad_handle;
+
+/* Fills *opts with the defaults listed above. */
+void lb_default_opts(lb_opts* opts);
+
+/* Device workspace, in bytes, that lindblad_setup needs for (n, d, opts).  Returns 0 for
+ * invalid sizes.  The caller allocates it (e.g. a torch uint8 tensor) and keeps it alive
+ * until lindblad_destroy. */
+size_t lindblad_workspace_bytes(int n, int d, const lb_opts* opts);
+
+/* Set-up, once per Lindbladian (Sec. 1.2 Eq. (3); App. A.1).
+ *   H_dev : n x n Hermitian Hamiltonian (device, complex128, row-major)
+ *   L_dev : d stacked n x n jump operators (device, d*n*n complex128)
+ * Copies H and L into the workspace, forms G = -iH - 1/2 sum_j L_j^dag L_j with one
+ * stacked GEMM, computes the Schur form G = Q T Q^dag (eigenvectors -> QR -> upper
+ * triangle of Q^dag G Q), the Schur-coordinate jump operators L~_j = Q^dag L_j Q and the
+ * case-1 test of Theorem 1.  On success *out receives a handle.
+ * Errors: LB_INVALID_ARG (n < 2, d < 1, null pointers), LB_WORKSPACE_TOO_SMALL,
+ * LB_SOLVER_ERROR, LB_CUDA_ERROR.  info (nullable) receives set-up diagnostics. */
+lb_status lindblad_setup(const void* H_dev, const void* L_dev, int n, int d,
+                         void* workspace_dev, size_t workspace_bytes, void* stream,
+                         const lb_opts* opts, lindblad_handle* out, lb_info* info);
+
+/* Y = Phi(X) = -K(S^{-1} X)  (Theorem 1, the map iterated by Alg. 4), or, with
+ * LB_APPLY_FORM_M, Y = M(X) = -S^{-1}(K X) (proof of Theorem 1).  X_dev, Y_dev: n x n
+ * device complex128; X is not modified; X and Y must not alias.  With LB_APPLY_SCHUR
+ * both are in Schur coordinates (what the Arnoldi loop iterates), otherwise in the
+ * original basis.  precision: lb_precision.  Errors: LB_INVALID_ARG, LB_S_SINGULAR
+ * (case 1: S not invertible), LB_CUDA_ERROR. */
+lb_status phi_apply(lindblad_handle h, const void* X_dev, void* Y_dev, int flags,
+                    int precision, void* stream);
+
+/* X = R_lam^S(Y) = (lam - S)^{-1}(Y), the no-jump resolvent (Sec. 3.1), by Bartels-Stewart
+ * on the stored Schur form with T -> T - lam/2 I (App. A.1.1).  lam = 0 gives -S^{-1}.
+ * Original-basis device operands.  Errors as phi_apply. */
+lb_status resolvent_apply(lindblad_handle h, const void* Y_dev, void* X_dev, double lam,
+                          int precision, void* stream);
+
+/* R = L(X) = G X + X G^dag + sum_j L_j X L_j^dag in FP64, original basis (Eq. (1)). */
+lb_status lindbladian_apply(lindblad_handle h, const void* X_dev, void* R_dev, void* stream);
+
+/* Steady state by Phi-Arnoldi (Alg. 4): explicitly restarted Arnoldi on Phi in Schur
+ * coordinates, Ritz value nearest 1, rho = -S^{-1} xi, hermitise + trace-normalise, stop when
+ * ||L(rho_hat)||_max < opts->tol (FP64, original basis).  With LB_PREC_MIXED the cycles run
+ * on tensor-core GEMMs and the state is then refined in FP64 (residual-correction steps,
+ * each a right-preconditioned GMRES solve of L~_eta delta = -r, Alg. 2/3).
+ *   rho_dev : n x n device output (Hermitian, trace 1).
+ * Returns LB_OK, LB_NOT_CONVERGED (best state returned), LB_S_SINGULAR (pure steady state of
+ * Theorem 1 case 1 returned), or an error. */
+lb_status steady_state(lindblad_handle h, void* rho_dev, const lb_opts* opts, lb_info* info,
+                       void* stream);
+
+/* The k smallest-|lambda| nonzero eigenvalues of L by shift-invert Arnoldi on
+ * (mu - L~_eta)^{-1} (Alg. 5), each application a GMRES solve right-preconditioned by
+ * Precond(., mu, eta) (Alg. 2).  Thick (Krylov-Schur) restarts keep opts->keep_ritz pairs;
+ * stop when max_k ||L v_k - lambda_k v_k||_max / ||v_k||_max < opts->tol.
+ *   evals_host : k complex128 (host memory), sorted by |lambda|, then Re descending.
+ *   evecs_dev  : nullable; k stacked n x n device eigenvectors (raw, traceless).
+ * Errors: LB_INVALID_ARG (k < 1 or k > m - 2), LB_ETA_EXCLUDED, LB_S_SINGULAR (mu = 0 with
+ * S singular), LB_NOT_CONVERGED (best estimates returned). */
+lb_status low_spectrum(lindblad_handle h, int k, double mu, double eta, void* evals_host,
+                       void* evecs_dev, const lb_opts* opts, lb_info* info, void* stream);
+
+/* Releases the host-side handle (the workspace stays the caller's). */
+void lindblad_destroy(lindblad_handle h);
+
+/* Human-readable name of a status code. */
+const char* lb_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif  /* LINDBLAD_H_ */

@@ -1,0 +1,85 @@
+// Internal state of a lindblad_handle and the host-side sequencing helpers shared between
+// lindblad.cu (set-up, Phi, Alg. 4), solvers.cu (GMRES, refinement, Alg. 5) and
+// mixed.cu (tensor-core path).
+#pragma once
+#include <functional>
+
+#include "../../include/lindblad.h"
+#include "common.cuh"
+
+#define LB_CHECK_CUDA(expr)                                                                 \
+    do {                                                                                    \
+        cudaError_t _e = (expr);                                                            \
+        if (_e != cudaSuccess) {                                                            \
+            fprintf(stderr, "lindblad: CUDA error %s at %s:%d\n", cudaGetErrorString(_e),   \
+                    __FILE__, __LINE__);                                                    \
+            return LB_CUDA_ERROR;                                                           \
+        }                                                                                   \
+    } while (0)
+
+constexpr int KMAX = 64;      // largest Krylov cycle (outer Arnoldi or inner GMRES)
+constexpr int NSCRATCH = 8;   // n x n scratch matrices
+
+struct MixedState;            // tensor-core path buffers (mixed.cu)
+
+struct lb_handle_s {
+    int n = 0, d = 0;
+    lb_opts opts{};
+    size_t ws_bytes = 0;
+    // FP64 problem data and factors (device)
+    cplx *H = nullptr, *L = nullptr, *G = nullptr, *Q = nullptr, *T = nullptr, *Lt = nullptr;
+    cplx* P = nullptr;                 // d n^2 scratch (jump-term intermediate)
+    cplx* X[NSCRATCH] = {};            // n x n scratch
+    cplx* best = nullptr;              // n x n
+    cplx* W = nullptr;                 // R_mu^S(I) for the Sherman-Morrison preconditioner
+    cplx* V = nullptr;                 // inner Krylov basis (vcap vectors)
+    cplx* Z = nullptr;                 // outer Krylov basis (vcap vectors)
+    int vcap = 0;
+    cplx* hm = nullptr;                // (KMAX+1) x (KMAX+1) column-major, ld = ldh (inner)
+    cplx* hm2 = nullptr;               // same, outer
+    int ldh = 0;
+    cplx* ev = nullptr;                // KMAX
+    cplx* evec = nullptr;              // KMAX x KMAX
+    cplx* small = nullptr;             // 4 (KMAX+2)
+    cplx* part = nullptr;              // DOT_BLOCKS (KMAX+2)
+    double* dpart = nullptr;           // 2 DOT_BLOCKS
+    double* dscal = nullptr;           // 16
+    cplx* scal = nullptr;              // 16
+    int* dinfo = nullptr;              // 16
+    char* solver_ws = nullptr;
+    size_t solver_ws_bytes = 0;
+    char* mixed_base = nullptr;
+    MixedState* mixed = nullptr;
+    bool mixed_ready = false;
+    // host-side diagnostics
+    double gnorm = 0.0, schur_err = 0.0, min_re_T = 0.0, setup_ms = 0.0;
+    int case1 = 0;
+    ~lb_handle_s();
+};
+
+typedef std::function<int(const cplx*, cplx*)> OpFn;
+
+// lindblad.cu
+int gemm(lb_handle_s* h, cudaStream_t s, cplx* C, const cplx* A, int opA, const cplx* B, int opB, int M, int N,
+         int K, cplx alpha, cplx beta);
+int jump_f64(lb_handle_s* h, cudaStream_t s, const cplx* Ls, const cplx* Z, cplx* Y, cplx alpha, cplx beta);
+int lindbladian_f64(lb_handle_s* h, cudaStream_t s, const cplx* X, cplx* R);
+int change_basis(lb_handle_s* h, cudaStream_t s, const cplx* X, cplx* Out, cplx* tmp, int to_schur);
+int lyap_schur(lb_handle_s* h, cudaStream_t s, const cplx* Y, cplx* X, double shift, int precision);
+int phi_schur(lb_handle_s* h, cudaStream_t s, const cplx* X, cplx* Y, int form, int precision);
+int arnoldi_cycle(lb_handle_s* h, cudaStream_t s, cplx* basis, cplx* hess, int j0, int m, const OpFn& op,
+                  int* k_out);
+int hermitize_normalize(lb_handle_s* h, cudaStream_t s, const cplx* in, cplx* out, cplx* tmp);
+int residual_norms(lb_handle_s* h, cudaStream_t s, const cplx* rho, cplx* R, double* rmax, double* rfro);
+lb_status steady_state_arnoldi(lb_handle_s* h, cudaStream_t s, const lb_opts& o, cplx* rho_out, lb_info* inf);
+
+// solvers.cu
+int pure_state_case1(lb_handle_s* h, cudaStream_t s, cplx* rho_out);
+lb_status refine_steady_state(lb_handle_s* h, cudaStream_t s, const lb_opts& o, cplx* rho, lb_info* inf);
+
+// mixed.cu
+size_t mixed_bytes(int n, int d);
+int mixed_prepare(lb_handle_s* h, cudaStream_t s);
+int jump_mixed(lb_handle_s* h, cudaStream_t s, const cplx* Z, cplx* Y, double alpha);
+int trisylv_mixed(lb_handle_s* h, cudaStream_t s, cplx* X, double shift);
+void mixed_release(lb_handle_s* h);

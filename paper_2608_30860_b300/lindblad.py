@@ -1,0 +1,202 @@
+"""Thin Python binding of liblindblad.so (include/lindblad.h): argument marshalling only.
+
+Torch is used for device memory (the caller-side workspace and result tensors) and for the
+current CUDA stream; every computation runs in the library's CUDA kernels.  The functions
+carry the C names: lindblad_workspace_bytes, lindblad_setup, phi_apply, resolvent_apply,
+lindbladian_apply, steady_state, low_spectrum, lindblad_destroy.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "liblindblad.so")
+
+LB_PREC_FP64 = 0
+LB_PREC_MIXED = 1
+LB_APPLY_FORM_M = 1
+LB_APPLY_SCHUR = 2
+
+STATUS = {0: "LB_OK", 1: "LB_NOT_CONVERGED", 2: "LB_S_SINGULAR", 3: "LB_ILL_CONDITIONED",
+          -1: "LB_INVALID_ARG", -2: "LB_CUDA_ERROR", -3: "LB_ETA_EXCLUDED",
+          -4: "LB_WORKSPACE_TOO_SMALL", -5: "LB_NOT_IMPLEMENTED", -6: "LB_SOLVER_ERROR"}
+
+
+class LindbladError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)}")
+
+
+class LbOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("krylov_m", ctypes.c_int), ("max_restarts", ctypes.c_int),
+                ("precision", ctypes.c_int), ("eta", ctypes.c_double), ("max_refine", ctypes.c_int),
+                ("gmres_m", ctypes.c_int), ("sylv_block", ctypes.c_int), ("inner_tol", ctypes.c_double),
+                ("keep_ritz", ctypes.c_int)]
+
+
+class LbInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("restarts", ctypes.c_int), ("phi_applies", ctypes.c_int),
+                ("gmres_steps", ctypes.c_int), ("refine_steps", ctypes.c_int),
+                ("residual_max", ctypes.c_double), ("residual_fro", ctypes.c_double),
+                ("ritz_value", ctypes.c_double), ("schur_backward_err", ctypes.c_double),
+                ("min_abs_re_T", ctypes.c_double), ("setup_ms", ctypes.c_double), ("solve_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Loads liblindblad.so; raises if it is missing (there is no fallback path)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} not found: build it with python -m paper_2608_30860_b300.build")
+    lib = ctypes.CDLL(path)
+    vp, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    P = ctypes.POINTER
+    lib.lb_default_opts.argtypes = [P(LbOpts)]
+    lib.lb_default_opts.restype = None
+    lib.lindblad_workspace_bytes.argtypes = [i, i, P(LbOpts)]
+    lib.lindblad_workspace_bytes.restype = sz
+    lib.lindblad_setup.argtypes = [vp, vp, i, i, vp, sz, vp, P(LbOpts), P(vp), P(LbInfo)]
+    lib.lindblad_setup.restype = i
+    lib.phi_apply.argtypes = [vp, vp, vp, i, i, vp]
+    lib.phi_apply.restype = i
+    lib.resolvent_apply.argtypes = [vp, vp, vp, d, i, vp]
+    lib.resolvent_apply.restype = i
+    lib.lindbladian_apply.argtypes = [vp, vp, vp, vp]
+    lib.lindbladian_apply.restype = i
+    lib.steady_state.argtypes = [vp, vp, P(LbOpts), P(LbInfo), vp]
+    lib.steady_state.restype = i
+    lib.low_spectrum.argtypes = [vp, i, d, d, vp, vp, P(LbOpts), P(LbInfo), vp]
+    lib.low_spectrum.restype = i
+    lib.lindblad_destroy.argtypes = [vp]
+    lib.lindblad_destroy.restype = None
+    lib.lb_status_string.argtypes = [i]
+    lib.lb_status_string.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def default_opts(**kw) -> LbOpts:
+    o = LbOpts()
+    load_library().lb_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dev(t: torch.Tensor, shape=None) -> int:
+    if not (t.is_cuda and t.dtype == torch.complex128 and t.is_contiguous()):
+        raise ValueError("expected a contiguous complex128 CUDA tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"expected shape {shape}, got {tuple(t.shape)}")
+    return t.data_ptr()
+
+
+@dataclass
+class Handle:
+    ptr: ctypes.c_void_p
+    n: int
+    d: int
+    workspace: torch.Tensor
+    setup_info: dict
+
+
+def lindblad_workspace_bytes(n: int, d: int, opts: LbOpts | None = None) -> int:
+    o = opts or default_opts()
+    return int(load_library().lindblad_workspace_bytes(n, d, ctypes.byref(o)))
+
+
+def lindblad_setup(H: torch.Tensor, L: torch.Tensor, opts: LbOpts | None = None) -> Handle:
+    """H: (n, n), L: (d, n, n) complex128 CUDA tensors.  Allocates the workspace with torch."""
+    lib = load_library()
+    n = H.shape[0]
+    d = L.shape[0]
+    o = opts or default_opts()
+    nbytes = lindblad_workspace_bytes(n, d, o)
+    if nbytes == 0:
+        raise LindbladError(-1, "lindblad_workspace_bytes")
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=H.device)
+    h = ctypes.c_void_p()
+    info = LbInfo()
+    st = lib.lindblad_setup(_dev(H, (n, n)), _dev(L, (d, n, n)), n, d, ws.data_ptr(), nbytes, _stream(),
+                            ctypes.byref(o), ctypes.byref(h), ctypes.byref(info))
+    if st < 0:
+        raise LindbladError(st, "lindblad_setup")
+    return Handle(h, n, d, ws, info.as_dict())
+
+
+def phi_apply(h: Handle, X: torch.Tensor, Y: torch.Tensor | None = None, form: str = "phi",
+              schur: bool = False, precision: int = LB_PREC_FP64) -> torch.Tensor:
+    """Y = Phi(X) = -K(S^{-1} X) (form='phi') or M(X) = -S^{-1}(K X) (form='M')."""
+    Y = torch.empty_like(X) if Y is None else Y
+    flags = (LB_APPLY_FORM_M if form.lower() == "m" else 0) | (LB_APPLY_SCHUR if schur else 0)
+    st = load_library().phi_apply(h.ptr, _dev(X, (h.n, h.n)), _dev(Y, (h.n, h.n)), flags, precision, _stream())
+    if st != 0:
+        raise LindbladError(st, "phi_apply")
+    return Y
+
+
+def resolvent_apply(h: Handle, Y: torch.Tensor, lam: float, precision: int = LB_PREC_FP64) -> torch.Tensor:
+    """X = (lam - S)^{-1}(Y)."""
+    X = torch.empty_like(Y)
+    st = load_library().resolvent_apply(h.ptr, _dev(Y, (h.n, h.n)), _dev(X), float(lam), precision, _stream())
+    if st != 0:
+        raise LindbladError(st, "resolvent_apply")
+    return X
+
+
+def lindbladian_apply(h: Handle, X: torch.Tensor) -> torch.Tensor:
+    R = torch.empty_like(X)
+    st = load_library().lindbladian_apply(h.ptr, _dev(X, (h.n, h.n)), _dev(R), _stream())
+    if st != 0:
+        raise LindbladError(st, "lindbladian_apply")
+    return R
+
+
+def steady_state(h: Handle, opts: LbOpts | None = None, rho: torch.Tensor | None = None):
+    """Returns (rho, info dict, status).  Raises on negative status."""
+    o = opts or default_opts()
+    rho = torch.empty((h.n, h.n), dtype=torch.complex128, device=h.workspace.device) if rho is None else rho
+    info = LbInfo()
+    st = load_library().steady_state(h.ptr, _dev(rho, (h.n, h.n)), ctypes.byref(o), ctypes.byref(info), _stream())
+    if st < 0:
+        raise LindbladError(st, "steady_state")
+    return rho, info.as_dict(), st
+
+
+def low_spectrum(h: Handle, k: int, mu: float = 0.0, eta: float = 1.0, want_vectors: bool = False,
+                 opts: LbOpts | None = None):
+    """Returns (evals complex128 CPU tensor (k,), evecs CUDA tensor (k, n, n) or None, info, status)."""
+    o = opts or default_opts()
+    ev = torch.zeros(k, dtype=torch.complex128)
+    vecs = torch.empty((k, h.n, h.n), dtype=torch.complex128, device=h.workspace.device) if want_vectors else None
+    info = LbInfo()
+    st = load_library().low_spectrum(h.ptr, k, float(mu), float(eta), ev.data_ptr(),
+                                     None if vecs is None else vecs.data_ptr(), ctypes.byref(o),
+                                     ctypes.byref(info), _stream())
+    if st < 0:
+        raise LindbladError(st, "low_spectrum")
+    return ev, vecs, info.as_dict(), st
+
+
+def lindblad_destroy(h: Handle):
+    if h.ptr:
+        load_library().lindblad_destroy(h.ptr)
+        h.ptr = ctypes.c_void_p()

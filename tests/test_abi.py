@@ -1,0 +1,60 @@
+"""The C-ABI library builds, loads without a GPU and exports every entry point that
+include/lindblad.h declares.  No compute calls (no GPU here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+
+
+HEADER = os.path.join(ROOT, "include", "lindblad.h")
+
+
+def _declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s+([a-z_][a-z0-9_]*)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2608_30860_b300.build import build
+    path = build(verbose=False)
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("lindblad_setup", "phi_apply", "steady_state", "low_spectrum", "lindblad_destroy",
+                     "lindblad_workspace_bytes", "resolvent_apply", "lindbladian_apply"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_opts_struct_layout_and_defaults(lib):
+    from paper_2608_30860_b300 import lindblad as B
+    o = B.default_opts()
+    assert o.tol == 1e-10 and o.krylov_m == 20 and o.eta == 1.0 and o.precision == B.LB_PREC_FP64
+    assert ctypes.sizeof(B.LbOpts) == 64   # C layout: 3 doubles, 7 ints, natural padding
+    assert ctypes.sizeof(B.LbInfo) == 80
+
+
+def test_invalid_sizes_rejected_on_host(lib):
+    from paper_2608_30860_b300 import lindblad as B
+    assert B.lindblad_workspace_bytes(1, 1) == 0
+    assert B.lindblad_workspace_bytes(8, 0) == 0
+    o = B.default_opts(krylov_m=200)
+    assert B.lindblad_workspace_bytes(8, 2, o) == 0
+
+
+def test_status_strings(lib):
+    lib.lb_status_string.restype = ctypes.c_char_p
+    assert lib.lb_status_string(-3) == b"LB_ETA_EXCLUDED"
+    assert lib.lb_status_string(2) == b"LB_S_SINGULAR"
