@@ -50,7 +50,7 @@ typedef enum {
 typedef enum {
     LB_PREC_FP64 = 0,   /* every contraction in FP64 on the CUDA cores */
     LB_PREC_MIXED = 1   /* jump-term and Sylvester-update GEMMs on the tensor cores (tcgen05,
-                           BF16 split, FP32 accumulate); FP64 Sylvester leaves, FP64 residual,
+                           split-FP16 operands, FP32 accumulate); FP64 residual,
                            FP64 iterative refinement of the steady state */
 } lb_precision;
 
@@ -68,9 +68,10 @@ typedef struct {
     int    precision;     /* lb_precision (default LB_PREC_FP64) */
     double eta;           /* deflation coefficient eta (default 1) */
     int    max_refine;    /* mixed precision: refinement steps cap (default 8) */
-    int    gmres_m;       /* inner GMRES cycle length (default 20) */
+    int    gmres_m;       /* inner GMRES cycle length (default 40) */
     int    sylv_block;    /* triangular Sylvester block size (default 0 = automatic) */
-    double inner_tol;     /* shift-invert inner GMRES relative tolerance (default 1e-12) */
+    double inner_tol;     /* shift-invert inner GMRES relative tolerance (default 1e-10); a solve also
+                             stops when one restart cycle reduces its residual by less than 10% */
     int    keep_ritz;     /* p of Alg. 5: Ritz pairs kept at a thick restart (default 0 = auto) */
 } lb_opts;
 
@@ -121,6 +122,13 @@ lb_status lindblad_setup(const void* H_dev, const void* L_dev, int n, int d,
 lb_status phi_apply(lindblad_handle h, const void* X_dev, void* Y_dev, int flags,
                     int precision, void* stream);
 
+/* Y = K(X) = sum_j L_j X L_j^dag, the jump part of Eq. (2) (the dominant contraction of every Phi
+ * application).  With LB_APPLY_SCHUR, X and Y are in Schur coordinates and L~_j = Q^dag L_j Q is
+ * used.  precision: LB_PREC_FP64 (CUDA-core FP64) or LB_PREC_MIXED (tcgen05 split-FP16 GEMMs,
+ * FP32 accumulation).  X_dev, Y_dev: n x n device complex128, must not alias. */
+lb_status jump_apply(lindblad_handle h, const void* X_dev, void* Y_dev, int flags, int precision,
+                     void* stream);
+
 /* X = R_lam^S(Y) = (lam - S)^{-1}(Y), the no-jump resolvent (Sec. 3.1), by Bartels-Stewart
  * on the stored Schur form with T -> T - lam/2 I (App. A.1.1).  lam = 0 gives -S^{-1}.
  * Original-basis device operands.  Errors as phi_apply. */
@@ -151,6 +159,18 @@ lb_status steady_state(lindblad_handle h, void* rho_dev, const lb_opts* opts, lb
  * S singular), LB_NOT_CONVERGED (best estimates returned). */
 lb_status low_spectrum(lindblad_handle h, int k, double mu, double eta, void* evals_host,
                        void* evecs_dev, const lb_opts* opts, lb_info* info, void* stream);
+
+/* Kernel timing (diagnostics, no effect on results).  While enabled, the library records CUDA
+ * events on the launching stream around every tensor-core GEMM launch (kernel id 0) and every
+ * FP64 GEMM launch of the residual (kernel id 1).  lb_kernel_stats synchronises the stream and
+ * returns the launch count, the summed event time in ms and the summed algorithmic flops
+ * (8 real flops per complex multiply-add) since the last lb_set_profiling call. */
+lb_status lb_set_profiling(lindblad_handle h, int enable);
+lb_status lb_kernel_stats(lindblad_handle h, int kernel, int* launches, double* total_ms,
+                          double* algorithmic_flops);
+
+/* Number of CUDA kernels this library has launched in this process so far (all handles). */
+long long lb_launch_count(void);
 
 /* Releases the host-side handle (the workspace stays the caller's). */
 void lindblad_destroy(lindblad_handle h);

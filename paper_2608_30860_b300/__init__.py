@@ -5,11 +5,11 @@ package is its thin binding.  Importing does not load the library; the first cal
 and raises if it has not been built (python -m paper_2608_30860_b300.build).
 """
 from .lindblad import (LB_APPLY_FORM_M, LB_APPLY_SCHUR, LB_PREC_FP64, LB_PREC_MIXED, Handle, LbInfo,
-                       LbOpts, LindbladError, default_opts, lindblad_destroy, lindblad_setup,
+                       LbOpts, LindbladError, default_opts, jump_apply, lb_kernel_stats, lb_launch_count, lb_set_profiling, lindblad_destroy, lindblad_setup,
                        lindblad_workspace_bytes, lindbladian_apply, load_library, low_spectrum,
                        phi_apply, resolvent_apply, steady_state)
 
 __all__ = ["LB_APPLY_FORM_M", "LB_APPLY_SCHUR", "LB_PREC_FP64", "LB_PREC_MIXED", "Handle", "LbInfo",
-           "LbOpts", "LindbladError", "default_opts", "lindblad_destroy", "lindblad_setup",
+           "LbOpts", "LindbladError", "default_opts", "jump_apply", "lb_kernel_stats", "lb_launch_count", "lb_set_profiling", "lindblad_destroy", "lindblad_setup",
            "lindblad_workspace_bytes", "lindbladian_apply", "load_library", "low_spectrum", "phi_apply",
            "resolvent_apply", "steady_state"]

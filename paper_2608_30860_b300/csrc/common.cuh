@@ -56,3 +56,6 @@ struct ZGemmArgs {
 
 // host launchers (defined in the .cu files)
 int zgemm_f64(const ZGemmArgs& a, cudaStream_t s);
+
+// counts every kernel launch issued by the library (lb_launch_count in the C ABI)
+void lb_note_launch();

@@ -95,6 +95,6 @@ __global__ void __launch_bounds__(256) zgemm_f64_kernel(ZGemmArgs a) {
 int zgemm_f64(const ZGemmArgs& a, cudaStream_t s) {
     if (a.M <= 0 || a.N <= 0) return 0;
     dim3 grid((a.N + BN - 1) / BN, (a.M + BM - 1) / BM, a.reduce ? 1 : a.batch);
-    zgemm_f64_kernel<<<grid, 256, 0, s>>>(a);
+    zgemm_f64_kernel<<<grid, 256, 0, s>>>(a); lb_note_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

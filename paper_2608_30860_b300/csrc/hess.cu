@@ -273,7 +273,7 @@ int small_schur(const cplx* A, int lda, int m, int hess_in, int order, int nsel,
                              3 * 64 * 64 * (int)sizeof(cplx));
         attr = true;
     }
-    k_small_schur<<<1, 32, smem, s>>>(A, lda, m, hess_in, order, nsel, evals, evecs, Tout, Zout, info);
+    k_small_schur<<<1, 32, smem, s>>>(A, lda, m, hess_in, order, nsel, evals, evecs, Tout, Zout, info); lb_note_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

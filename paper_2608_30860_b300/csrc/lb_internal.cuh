@@ -3,6 +3,7 @@
 // mixed.cu (tensor-core path).
 #pragma once
 #include <functional>
+#include <vector>
 
 #include "../../include/lindblad.h"
 #include "common.cuh"
@@ -50,16 +51,24 @@ struct lb_handle_s {
     size_t solver_ws_bytes = 0;
     char* mixed_base = nullptr;
     MixedState* mixed = nullptr;
-    bool mixed_ready = false;
+    bool mixed_ready = false;         // tensor-core jump term available
+    bool mixed_sylv_ready = false;    // tensor-core triangular Sylvester available
     // host-side diagnostics
     double gnorm = 0.0, schur_err = 0.0, min_re_T = 0.0, setup_ms = 0.0;
     int case1 = 0;
+    // kernel timing (lb_set_profiling): event pairs and algorithmic flops per kernel id
+    bool profiling = false;
+    std::vector<cudaEvent_t> prof_ev[2];
+    std::vector<double> prof_flops[2];
     ~lb_handle_s();
 };
 
 typedef std::function<int(const cplx*, cplx*)> OpFn;
 
 // lindblad.cu
+// kernel timing hooks: record an event pair around a launch when profiling is on
+void prof_begin(lb_handle_s* h, cudaStream_t s, int kid);
+void prof_end(lb_handle_s* h, cudaStream_t s, int kid, double flops);
 int gemm(lb_handle_s* h, cudaStream_t s, cplx* C, const cplx* A, int opA, const cplx* B, int opB, int M, int N,
          int K, cplx alpha, cplx beta);
 int jump_f64(lb_handle_s* h, cudaStream_t s, const cplx* Ls, const cplx* Z, cplx* Y, cplx alpha, cplx beta);
@@ -71,6 +80,7 @@ int arnoldi_cycle(lb_handle_s* h, cudaStream_t s, cplx* basis, cplx* hess, int j
                   int* k_out);
 int hermitize_normalize(lb_handle_s* h, cudaStream_t s, const cplx* in, cplx* out, cplx* tmp);
 int residual_norms(lb_handle_s* h, cudaStream_t s, const cplx* rho, cplx* R, double* rmax, double* rfro);
+lb_status check_device_error(lb_handle_s* h, cudaStream_t s);
 lb_status steady_state_arnoldi(lb_handle_s* h, cudaStream_t s, const lb_opts& o, cplx* rho_out, lb_info* inf);
 
 // solvers.cu
@@ -79,6 +89,7 @@ lb_status refine_steady_state(lb_handle_s* h, cudaStream_t s, const lb_opts& o, 
 
 // mixed.cu
 size_t mixed_bytes(int n, int d);
+size_t mixed_P_rows(int n, int d);
 int mixed_prepare(lb_handle_s* h, cudaStream_t s);
 int jump_mixed(lb_handle_s* h, cudaStream_t s, const cplx* Z, cplx* Y, double alpha);
 int trisylv_mixed(lb_handle_s* h, cudaStream_t s, cplx* X, double shift);

@@ -5,6 +5,7 @@
 #include <cusolverDn.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <complex>
@@ -34,7 +35,7 @@ struct Carver {
 
 int krylov_cap(const lb_opts* o) {
     int m = o ? o->krylov_m : 20;
-    int g = o ? o->gmres_m : 20;
+    int g = o ? o->gmres_m : 40;
     return std::max(std::max(m, g), 4);
 }
 
@@ -68,7 +69,7 @@ void layout(lb_handle_s* h, char* base, int n, int d, const lb_opts* o, size_t s
     h->Q = c.take<cplx>(nn);
     h->T = c.take<cplx>(nn);
     h->Lt = c.take<cplx>((size_t)d * nn);
-    h->P = c.take<cplx>((size_t)d * nn);
+    h->P = c.take<cplx>(std::max((size_t)d * nn, mixed_P_rows(n, d) * (size_t)n));
     for (int i = 0; i < NSCRATCH; ++i) h->X[i] = c.take<cplx>(nn);
     h->best = c.take<cplx>(nn);
     h->W = c.take<cplx>(nn);
@@ -94,8 +95,36 @@ void layout(lb_handle_s* h, char* base, int n, int d, const lb_opts* o, size_t s
 
 }  // namespace
 
+// ============================================================================ launch counter
+static std::atomic<long long> g_launches{0};
+void lb_note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// ============================================================================ kernel timing
+void prof_begin(lb_handle_s* h, cudaStream_t s, int kid) {
+    if (!h->profiling) return;
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    cudaEventRecord(e, s);
+    h->prof_ev[kid].push_back(e);
+}
+void prof_end(lb_handle_s* h, cudaStream_t s, int kid, double flops) {
+    if (!h->profiling) return;
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    cudaEventRecord(e, s);
+    h->prof_ev[kid].push_back(e);
+    h->prof_flops[kid].push_back(flops);
+}
+static void prof_clear(lb_handle_s* h) {
+    for (int k = 0; k < 2; ++k) {
+        for (cudaEvent_t e : h->prof_ev[k]) cudaEventDestroy(e);
+        h->prof_ev[k].clear();
+        h->prof_flops[k].clear();
+    }
+}
+
 // ============================================================================ GEMM shorthands
-int gemm(lb_handle_s*, cudaStream_t s, cplx* C, const cplx* A, int opA, const cplx* B, int opB, int M, int N,
+int gemm(lb_handle_s* h, cudaStream_t s, cplx* C, const cplx* A, int opA, const cplx* B, int opB, int M, int N,
          int K, cplx alpha, cplx beta) {
     ZGemmArgs a{};
     a.M = M; a.N = N; a.K = K;
@@ -103,7 +132,10 @@ int gemm(lb_handle_s*, cudaStream_t s, cplx* C, const cplx* A, int opA, const cp
     a.B = B; a.ldb = (opB == OP_N) ? N : K; a.strideB = 0; a.opB = opB;
     a.C = C; a.ldc = N; a.strideC = 0;
     a.alpha = alpha; a.beta = beta; a.batch = 1; a.reduce = 1;
-    return zgemm_f64(a, s);
+    prof_begin(h, s, 1);
+    int r = zgemm_f64(a, s);
+    prof_end(h, s, 1, 8.0 * M * (double)N * K);
+    return r;
 }
 
 // Y = alpha * sum_j Lop_j Z Lop_j^dag + beta Y, with Lop the stack Ls (d x n x n), in FP64.
@@ -119,7 +151,10 @@ int jump_f64(lb_handle_s* h, cudaStream_t s, const cplx* Ls, const cplx* Z, cplx
     a.B = Ls; a.ldb = n; a.strideB = nn; a.opB = OP_C;
     a.C = Y; a.ldc = n; a.strideC = 0;
     a.alpha = alpha; a.beta = beta; a.batch = d; a.reduce = 1;
-    return zgemm_f64(a, s);
+    prof_begin(h, s, 1);
+    int r = zgemm_f64(a, s);
+    prof_end(h, s, 1, 8.0 * n * (double)n * n * d);
+    return r;
 }
 
 // R = L(X) = G X + X G^dag + sum_j L_j X L_j^dag, FP64, original basis
@@ -145,7 +180,7 @@ int change_basis(lb_handle_s* h, cudaStream_t s, const cplx* X, cplx* Out, cplx*
 int lyap_schur(lb_handle_s* h, cudaStream_t s, const cplx* Y, cplx* X, double shift, int precision) {
     const long long nn = (long long)h->n * h->n;
     if (X != Y) LB_CHECK_CUDA(cudaMemcpyAsync(X, Y, nn * sizeof(cplx), cudaMemcpyDeviceToDevice, s));
-    if (precision == LB_PREC_MIXED && h->mixed_ready) return trisylv_mixed(h, s, X, shift);
+    if (precision == LB_PREC_MIXED && h->mixed_sylv_ready) return trisylv_mixed(h, s, X, shift);
     return trisylv_f64(h->T, X, h->n, cmake(shift, 0.0), s);
 }
 
@@ -245,6 +280,19 @@ int residual_norms(lb_handle_s* h, cudaStream_t s, const cplx* rho, cplx* R, dou
     return 0;
 }
 
+// reads (and clears) the device error word set by bounded waits in the tensor-core kernels
+lb_status check_device_error(lb_handle_s* h, cudaStream_t s) {
+    int e = 0;
+    LB_CHECK_CUDA(cudaMemcpyAsync(&e, h->dinfo + 8, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LB_CHECK_CUDA(cudaStreamSynchronize(s));
+    if (e != 0) {
+        fprintf(stderr, "lindblad: tensor-core kernel wait timed out (code %d)\n", e);
+        cudaMemsetAsync(h->dinfo + 8, 0, sizeof(int), s);
+        return LB_CUDA_ERROR;
+    }
+    return LB_OK;
+}
+
 // ============================================================================ C ABI
 extern "C" {
 
@@ -256,9 +304,9 @@ void lb_default_opts(lb_opts* o) {
     o->precision = LB_PREC_FP64;
     o->eta = 1.0;
     o->max_refine = 8;
-    o->gmres_m = 20;
+    o->gmres_m = 40;
     o->sylv_block = 0;
-    o->inner_tol = 1e-12;
+    o->inner_tol = 1e-10;
     o->keep_ritz = 0;
 }
 
@@ -414,6 +462,7 @@ lb_status lindblad_setup(const void* H_dev, const void* L_dev, int n, int d, voi
     h->schur_err = diag[1] / std::max(diag[3], 1e-300);
     h->min_re_T = diag[4];
     h->case1 = h->min_re_T <= 1e3 * 2.220446049250313e-16 * h->gnorm;
+    if (cudaMemsetAsync(h->dinfo, 0, 16 * sizeof(int), s) != cudaSuccess) return fail(LB_CUDA_ERROR);
     if (mixed_prepare(h, s)) return fail(LB_CUDA_ERROR);
     if (cudaStreamSynchronize(s) != cudaSuccess) return fail(LB_CUDA_ERROR);
     h->setup_ms = now_ms() - t0;
@@ -428,7 +477,36 @@ lb_status lindblad_setup(const void* H_dev, const void* L_dev, int n, int d, voi
     return LB_OK;
 }
 
-void lindblad_destroy(lindblad_handle h) { delete h; }
+void lindblad_destroy(lindblad_handle h) {
+    if (h) prof_clear(h);
+    delete h;
+}
+
+long long lb_launch_count(void) { return g_launches.load(); }
+
+lb_status lb_set_profiling(lindblad_handle h, int enable) {
+    if (!h) return LB_INVALID_ARG;
+    prof_clear(h);
+    h->profiling = enable != 0;
+    return LB_OK;
+}
+
+lb_status lb_kernel_stats(lindblad_handle h, int kernel, int* launches, double* total_ms, double* flops) {
+    if (!h || kernel < 0 || kernel > 1) return LB_INVALID_ARG;
+    const auto& ev = h->prof_ev[kernel];
+    double ms = 0.0, fl = 0.0;
+    for (size_t i = 0; i + 1 < ev.size(); i += 2) {
+        LB_CHECK_CUDA(cudaEventSynchronize(ev[i + 1]));
+        float t = 0.f;
+        LB_CHECK_CUDA(cudaEventElapsedTime(&t, ev[i], ev[i + 1]));
+        ms += t;
+    }
+    for (double f : h->prof_flops[kernel]) fl += f;
+    if (launches) *launches = (int)(ev.size() / 2);
+    if (total_ms) *total_ms = ms;
+    if (flops) *flops = fl;
+    return LB_OK;
+}
 
 
 lb_status phi_apply(lindblad_handle h, const void* X_dev, void* Y_dev, int flags, int precision, void* stream) {
@@ -439,11 +517,35 @@ lb_status phi_apply(lindblad_handle h, const void* X_dev, void* Y_dev, int flags
     const cplx* X = (const cplx*)X_dev;
     cplx* Y = (cplx*)Y_dev;
     if (precision == LB_PREC_MIXED && !h->mixed_ready) return LB_NOT_IMPLEMENTED;
-    if (flags & LB_APPLY_SCHUR) return phi_schur(h, s, X, Y, form, precision) ? LB_CUDA_ERROR : LB_OK;
-    if (change_basis(h, s, X, h->X[1], h->X[2], 1)) return LB_CUDA_ERROR;
-    if (phi_schur(h, s, h->X[1], h->X[3], form, precision)) return LB_CUDA_ERROR;
-    if (change_basis(h, s, h->X[3], Y, h->X[2], 0)) return LB_CUDA_ERROR;
-    return LB_OK;
+    if (flags & LB_APPLY_SCHUR) {
+        if (phi_schur(h, s, X, Y, form, precision)) return LB_CUDA_ERROR;
+    } else {
+        if (change_basis(h, s, X, h->X[1], h->X[2], 1)) return LB_CUDA_ERROR;
+        if (phi_schur(h, s, h->X[1], h->X[3], form, precision)) return LB_CUDA_ERROR;
+        if (change_basis(h, s, h->X[3], Y, h->X[2], 0)) return LB_CUDA_ERROR;
+    }
+    return precision == LB_PREC_MIXED ? check_device_error(h, s) : LB_OK;
+}
+
+lb_status jump_apply(lindblad_handle h, const void* X_dev, void* Y_dev, int flags, int precision, void* stream) {
+    if (!h || !X_dev || !Y_dev || X_dev == Y_dev) return LB_INVALID_ARG;
+    if (precision == LB_PREC_MIXED && !h->mixed_ready) return LB_NOT_IMPLEMENTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    const cplx* X = (const cplx*)X_dev;
+    cplx* Y = (cplx*)Y_dev;
+    if (!(flags & LB_APPLY_SCHUR)) {
+        // original basis: L_j themselves (FP64), or via Schur coordinates on the tensor cores
+        if (precision != LB_PREC_MIXED) return jump_f64(h, s, h->L, X, Y, cmake(1, 0), cmake(0, 0)) ? LB_CUDA_ERROR : LB_OK;
+        if (change_basis(h, s, X, h->X[1], h->X[2], 1)) return LB_CUDA_ERROR;
+        if (jump_mixed(h, s, h->X[1], h->X[3], 1.0)) return LB_CUDA_ERROR;
+        if (change_basis(h, s, h->X[3], Y, h->X[2], 0)) return LB_CUDA_ERROR;
+        return check_device_error(h, s);
+    }
+    if (precision == LB_PREC_MIXED) {
+        if (jump_mixed(h, s, X, Y, 1.0)) return LB_CUDA_ERROR;
+        return check_device_error(h, s);
+    }
+    return jump_f64(h, s, h->Lt, X, Y, cmake(1, 0), cmake(0, 0)) ? LB_CUDA_ERROR : LB_OK;
 }
 
 lb_status resolvent_apply(lindblad_handle h, const void* Y_dev, void* X_dev, double lam, int precision,
@@ -538,6 +640,8 @@ lb_status steady_state_arnoldi(lb_handle_s* h, cudaStream_t s, const lb_opts& o,
         if (lyap_schur(h, s, xi, rt, 0.0, prec)) return LB_CUDA_ERROR;
         if (hermitize_normalize(h, s, rt, rt, R)) return LB_CUDA_ERROR;
         if (change_basis(h, s, rt, rho, R, 0)) return LB_CUDA_ERROR;
+        // the returned state is hermitised and trace-normalised in the original basis
+        if (hermitize_normalize(h, s, rho, rho, R)) return LB_CUDA_ERROR;
         double rmax, rfro;
         if (residual_norms(h, s, rho, R, &rmax, &rfro)) return LB_CUDA_ERROR;
         if (rmax < best) {

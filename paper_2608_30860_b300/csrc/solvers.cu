@@ -183,7 +183,7 @@ static int precond_apply(lb_handle_s* h, cudaStream_t s, const cplx* X, cplx* ou
     if (vec_scale_copy(out, X, nn, cmake(-1, 0), s)) return -1;                // -X
     if (lyap_schur(h, s, out, out, 0.5 * mu, precision)) return -1;            // Z
     if (mat_trace(out, h->n, h->scal + 9, s)) return -1;
-    k_sm_combine<<<grid1(nn), 256, 0, s>>>(out, h->W, nn, h->scal + 9, h->scal + 8, eta);
+    k_sm_combine<<<grid1(nn), 256, 0, s>>>(out, h->W, nn, h->scal + 9, h->scal + 8, eta); lb_note_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -229,13 +229,15 @@ static int gmres_solve(lb_handle_s* h, cudaStream_t s, const cplx* b, cplx* x, d
         if (vec_axpby(r, tmp, nn, cmake(-1, 0), cmake(1, 0), s)) return -1;
         if (vec_norms(r, nn, h->dpart, h->dscal, s)) return -1;
         double beta = read_double(s, h->dscal + 1);
+        const double prev = res;
         res = beta;
         if (!(beta > atol)) break;
+        if (cyc > 0 && beta > 0.9 * prev) break;   // stagnation: a cycle gained less than 10%
         if (vec_scale_copy(r, r, nn, cmake(1.0 / beta, 0), s)) return -1;
         int k = 0;
         if (arnoldi_cycle(h, s, h->V, h->hm, 0, m, op, &k)) return -1;
         *steps += k;
-        k_hess_lstsq<<<1, 32, 0, s>>>(h->hm, h->ldh, k, beta, h->evec, y, dres);
+        k_hess_lstsq<<<1, 32, 0, s>>>(h->hm, h->ldh, k, beta, h->evec, y, dres); lb_note_launch();
         if (vec_gemv(tmp, h->V, nn, k, y, nn, 1.0, 0, s)) return -1;      // u = V y
         if (precond_apply(h, s, tmp, pv, mu, eta, precision)) return -1;   // P u
         if (vec_axpby(x, pv, nn, cmake(1, 0), cmake(1, 0), s)) return -1;
@@ -249,10 +251,10 @@ int pure_state_case1(lb_handle_s* h, cudaStream_t s, cplx* rho_out) {
     const int n = h->n;
     cplx* v = h->X[0];
     cplx* psi = h->X[1];
-    k_case1_vector<<<1, 256, 0, s>>>(h->T, n, v);
+    k_case1_vector<<<1, 256, 0, s>>>(h->T, n, v); lb_note_launch();
     if (gemm(h, s, psi, h->Q, OP_N, v, OP_N, n, 1, n, cmake(1, 0), cmake(0, 0))) return -1;
     if (vec_dot_block(psi, n, 1, psi, n, h->scal + 3, h->part, 0, s)) return -1;
-    k_outer<<<grid1((long long)n * n), 256, 0, s>>>(rho_out, psi, n, h->scal + 3);
+    k_outer<<<grid1((long long)n * n), 256, 0, s>>>(rho_out, psi, n, h->scal + 3); lb_note_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -284,6 +286,7 @@ lb_status refine_steady_state(lb_handle_s* h, cudaStream_t s, const lb_opts& o, 
         if (vec_axpby(rs, delta, nn, cmake(1, 0), cmake(1, 0), s)) return LB_CUDA_ERROR;
         if (hermitize_normalize(h, s, rs, rs, h->X[4])) return LB_CUDA_ERROR;
         if (change_basis(h, s, rs, rho, h->X[4], 0)) return LB_CUDA_ERROR;
+        if (hermitize_normalize(h, s, rho, rho, h->X[4])) return LB_CUDA_ERROR;
         if (residual_norms(h, s, rho, R, &rmax, &rfro)) return LB_CUDA_ERROR;
     }
     inf->residual_max = rmax;
@@ -315,7 +318,7 @@ extern "C" lb_status low_spectrum(lindblad_handle h, int k, double mu, double et
     if (st != LB_OK) return st;
     // start vector: traceless, unit norm
     cplx* Zb = h->Z;
-    k_start_vector<<<grid1(nn), 256, 0, s>>>(Zb, n, 12345u);
+    k_start_vector<<<grid1(nn), 256, 0, s>>>(Zb, n, 12345u); lb_note_launch();
     if (mat_trace(Zb, n, h->scal + 4, s)) return LB_CUDA_ERROR;
     if (mat_add_diag_dev(Zb, n, h->scal + 4, -1.0 / n, s)) return LB_CUDA_ERROR;
     if (vec_norms(Zb, nn, h->dpart, h->dscal, s)) return LB_CUDA_ERROR;
@@ -404,7 +407,7 @@ extern "C" lb_status low_spectrum(lindblad_handle h, int k, double mu, double et
         LB_CHECK_CUDA(cudaMemcpyAsync(Zb, h->V, (size_t)p * nn * sizeof(cplx), cudaMemcpyDeviceToDevice, s));
         LB_CHECK_CUDA(cudaMemcpyAsync(Zb + (size_t)p * nn, Zb + (size_t)mm * nn, nn * sizeof(cplx),
                                       cudaMemcpyDeviceToDevice, s));
-        k_ks_restart<<<1, 256, 0, s>>>(h->hm2, h->ldh, Ts, Zs, mm, p);
+        k_ks_restart<<<1, 256, 0, s>>>(h->hm2, h->ldh, Ts, Zs, mm, p); lb_note_launch();
         j0 = p;
         st = LB_NOT_CONVERGED;
     }

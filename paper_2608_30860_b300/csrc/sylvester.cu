@@ -167,7 +167,7 @@ int trisylv_f64(const cplx* T, cplx* X, int n, cplx s, cudaStream_t st) {
         int lo = w - (nb - 1) > 0 ? w - (nb - 1) : 0;
         int hi = w < nb - 1 ? w : nb - 1;
         int cnt = hi - lo + 1;
-        trisylv_f64_wave<<<cnt, SYL_THREADS, smem, st>>>(T, X, n, s, w, nb);
+        trisylv_f64_wave<<<cnt, SYL_THREADS, smem, st>>>(T, X, n, s, w, nb); lb_note_launch();
     }
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

@@ -1,0 +1,70 @@
+// Tensor-core complex GEMM on split FP16 planes (sm_103a: TMA + tcgen05.mma + TMEM).
+//
+// An FP64 complex matrix X is stored for the tensor cores as four FP16 planes
+// [re_hi, re_lo, im_hi, im_lo] with X ~ 2^-e (hi + lo) (e a per-matrix power-of-two scale),
+// so that each product term carries ~22 significant bits.  One complex product over K is
+// accumulated in FP32 in TMEM as
+//     Dr += Ar Br^T - Ai Bi^T,   Di += Ar Bi^T + Ai Br^T
+// over the split pairs (hi,hi), (hi,lo), (lo,hi) -- the "4-real" complex product, three
+// split terms each.  Operands are K-major (row r of a plane holds op(X)[r, 0..K)).
+#pragma once
+#include <cuda.h>
+#include <cuda_fp16.h>
+
+#include "common.cuh"
+
+namespace tc {
+
+constexpr int BM = 128;   // tile rows (MMA M)
+constexpr int BN = 128;   // tile cols (MMA N)
+constexpr int BK = 64;    // K per stage: 64 fp16 = one 128-byte swizzle row
+constexpr int STAGES = 3;
+constexpr int TILE_BYTES = BM * BK * 2;              // 16 KiB (BM == BN)
+constexpr int STAGE_BYTES = 4 * TILE_BYTES;          // A re, A im, B re, B im
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int MAX_SEGS = 2;
+
+// sign conventions of one segment
+enum { SIGN_NORMAL = 0, SIGN_CONJ_B = 1, SIGN_CONJ_A = 2 };
+
+struct Seg {
+    int a_map, b_map;        // tensor-map slots
+    int a_row, b_row;        // row-coordinate offsets added to the tile origin (m0 / n0)
+    int a_j, b_j;            // batch (dim 2) coordinate of the first K-batch
+    int a_jstep, b_jstep;    // batch step per K-batch
+    int nbatch;              // number of K-batches
+    int k0, klen;            // K range (dim 0) within each batch
+    int sign;                // SIGN_*
+};
+
+struct Maps {
+    CUtensorMap m[4];
+};
+
+struct Params {
+    int M, N;                // output extent (rows, cols) -- masks the epilogue
+    int nseg;
+    Seg seg[MAX_SEGS];
+    int npairs;              // 1: (hi,hi) only; 3: (hi,hi),(hi,lo),(lo,hi)
+    // epilogue: out[r * ldo + c] = alpha * scale[0] * (Dr + i Di) (+ beta * out)
+    cplx* out;
+    long long ldo;
+    double alpha;
+    const double* scale;     // device scalar (product of the operands' inverse scales), nullable
+    int accumulate;          // 1: out += result
+    int* err;                // device error word (set on a wait timeout)
+};
+
+}  // namespace tc
+
+// host-side helpers (tc_gemm.cu)
+// planes: 4 * nbatch * rows * ld halves, plane-major; builds a 4D map (K, rows, nbatch, 4)
+int tc_make_map(CUtensorMap* map, const __half* planes, int K, int rows, int nbatch, int ld);
+int tc_gemm_launch(const tc::Maps& maps, const tc::Params& p, int grid_m, int grid_n, cudaStream_t s);
+// X (complex128, rows x cols, ld_src) -> 4 FP16 planes (rows x ld_dst, plane stride pstride),
+// element op: transpose (op = 1) / conjugate (conj = 1); value scaled by scale_dev[0].
+int tc_split_planes(const cplx* X, long long ld_src, int rows, int cols, int transpose, int conj,
+                    const double* scale_dev, __half* planes, int ld_dst, long long pstride, int batch,
+                    long long src_bstride, long long dst_bstride, cudaStream_t s);
+// scale_dev[0] = 2^e with 2^e * maxabs <= 2^14 ; inv_dev[0] = 2^-e  (maxabs from vec_norms)
+int tc_pick_scale(const double* maxabs_dev, double* scale_dev, double* inv_dev, cudaStream_t s);

@@ -261,81 +261,81 @@ int vec_dot_block(const cplx* V, long long vstride, int k, const cplx* w, long l
                   cplx* partial, int accumulate, cudaStream_t s) {
     const int nblk = DOT_BLOCKS;
     dim3 grid(nblk, (k + KB - 1) / KB);
-    k_block_dot<<<grid, RT, 0, s>>>(V, vstride, k, w, len, partial);
-    k_reduce_partials<<<1, 128, 0, s>>>(partial, nblk, k, out, accumulate);
+    k_block_dot<<<grid, RT, 0, s>>>(V, vstride, k, w, len, partial); lb_note_launch();
+    k_reduce_partials<<<1, 128, 0, s>>>(partial, nblk, k, out, accumulate); lb_note_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 int vec_gemv(cplx* y, const cplx* V, long long vstride, int k, const cplx* h, long long len, double sign,
              int keep_y, cudaStream_t s) {
-    k_gemv<<<grid_for(len), RT, 0, s>>>(y, V, vstride, k, h, len, sign, keep_y);
+    k_gemv<<<grid_for(len), RT, 0, s>>>(y, V, vstride, k, h, len, sign, keep_y); lb_note_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 int vec_finish_column(cplx* hcol, const cplx* h2, int k, const cplx* nrm2, cplx* inv, cudaStream_t s) {
-    k_finish_column<<<1, 128, 0, s>>>(hcol, h2, k, nrm2, inv);
+    k_finish_column<<<1, 128, 0, s>>>(hcol, h2, k, nrm2, inv); lb_note_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 int vec_scale_dev(cplx* x, long long len, const cplx* a, cudaStream_t s) {
-    k_scale_dev<<<grid_for(len), RT, 0, s>>>(x, len, a);
+    k_scale_dev<<<grid_for(len), RT, 0, s>>>(x, len, a); lb_note_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 int vec_scale_copy(cplx* y, const cplx* x, long long len, cplx a, cudaStream_t s) {
-    k_scale_copy<<<grid_for(len), RT, 0, s>>>(y, x, len, a);
+    k_scale_copy<<<grid_for(len), RT, 0, s>>>(y, x, len, a); lb_note_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 int vec_axpby(cplx* y, const cplx* x, long long len, cplx a, cplx b, cudaStream_t s) {
-    k_axpby<<<grid_for(len), RT, 0, s>>>(y, x, len, a, b);
+    k_axpby<<<grid_for(len), RT, 0, s>>>(y, x, len, a, b); lb_note_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 int mat_trace(const cplx* X, int n, cplx* out, cudaStream_t s) {
-    k_trace<<<1, 256, 0, s>>>(X, n, out);
+    k_trace<<<1, 256, 0, s>>>(X, n, out); lb_note_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 int mat_div_by_dev(cplx* out, const cplx* X, long long len, const cplx* tr, cudaStream_t s, int real_only) {
-    k_div_by_dev<<<grid_for(len), RT, 0, s>>>(out, X, len, tr, real_only);
+    k_div_by_dev<<<grid_for(len), RT, 0, s>>>(out, X, len, tr, real_only); lb_note_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 int mat_hermitize(cplx* Y, const cplx* X, int n, cudaStream_t s) {
-    k_hermitize<<<grid_for((long long)n * n), RT, 0, s>>>(Y, X, n);
+    k_hermitize<<<grid_for((long long)n * n), RT, 0, s>>>(Y, X, n); lb_note_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 int vec_norms(const cplx* x, long long len, double* part, double* out, cudaStream_t s) {
-    k_norms_partial<<<DOT_BLOCKS, RT, 0, s>>>(x, len, part);
-    k_norms_final<<<1, 32, 0, s>>>(part, DOT_BLOCKS, out);
+    k_norms_partial<<<DOT_BLOCKS, RT, 0, s>>>(x, len, part); lb_note_launch();
+    k_norms_final<<<1, 32, 0, s>>>(part, DOT_BLOCKS, out); lb_note_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 int mat_eye(cplx* X, int n, cplx a, cudaStream_t s) {
-    k_eye<<<grid_for((long long)n * n), RT, 0, s>>>(X, n, a);
+    k_eye<<<grid_for((long long)n * n), RT, 0, s>>>(X, n, a); lb_note_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 int mat_add_diag_dev(cplx* X, int n, const cplx* a, double scale, cudaStream_t s) {
-    k_add_diag_dev<<<(n + 255) / 256, 256, 0, s>>>(X, n, a, scale);
+    k_add_diag_dev<<<(n + 255) / 256, 256, 0, s>>>(X, n, a, scale); lb_note_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 int mat_transpose(cplx* Y, const cplx* X, int n, cudaStream_t s) {
     dim3 g((n + 31) / 32, (n + 31) / 32);
-    k_transpose<<<g, dim3(32, 8), 0, s>>>(Y, X, n);
+    k_transpose<<<g, dim3(32, 8), 0, s>>>(Y, X, n); lb_note_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 int mat_take_upper(cplx* T, const cplx* A, int n, double* part, double* out, cudaStream_t s) {
-    k_take_upper<<<DOT_BLOCKS, RT, 0, s>>>(T, A, n, part);
-    k_norms_final<<<1, 32, 0, s>>>(part, DOT_BLOCKS, out);
+    k_take_upper<<<DOT_BLOCKS, RT, 0, s>>>(T, A, n, part); lb_note_launch();
+    k_norms_final<<<1, 32, 0, s>>>(part, DOT_BLOCKS, out); lb_note_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 int mat_min_abs_re_diag(const cplx* T, int n, double* out, cudaStream_t s) {
-    k_min_abs_re_diag<<<1, 256, 0, s>>>(T, n, out);
+    k_min_abs_re_diag<<<1, 256, 0, s>>>(T, n, out); lb_note_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

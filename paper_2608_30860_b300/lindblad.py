@@ -71,6 +71,8 @@ def load_library(path: str = LIB_PATH):
     lib.lindblad_setup.restype = i
     lib.phi_apply.argtypes = [vp, vp, vp, i, i, vp]
     lib.phi_apply.restype = i
+    lib.jump_apply.argtypes = [vp, vp, vp, i, i, vp]
+    lib.jump_apply.restype = i
     lib.resolvent_apply.argtypes = [vp, vp, vp, d, i, vp]
     lib.resolvent_apply.restype = i
     lib.lindbladian_apply.argtypes = [vp, vp, vp, vp]
@@ -81,6 +83,12 @@ def load_library(path: str = LIB_PATH):
     lib.low_spectrum.restype = i
     lib.lindblad_destroy.argtypes = [vp]
     lib.lindblad_destroy.restype = None
+    lib.lb_set_profiling.argtypes = [vp, i]
+    lib.lb_set_profiling.restype = i
+    lib.lb_kernel_stats.argtypes = [vp, i, P(i), P(d), P(d)]
+    lib.lb_kernel_stats.restype = i
+    lib.lb_launch_count.argtypes = []
+    lib.lb_launch_count.restype = ctypes.c_longlong
     lib.lb_status_string.argtypes = [i]
     lib.lb_status_string.restype = ctypes.c_char_p
     _lib = lib
@@ -153,6 +161,17 @@ def phi_apply(h: Handle, X: torch.Tensor, Y: torch.Tensor | None = None, form: s
     return Y
 
 
+def jump_apply(h: Handle, X: torch.Tensor, Y: torch.Tensor | None = None, schur: bool = False,
+               precision: int = LB_PREC_FP64) -> torch.Tensor:
+    """Y = K(X) = sum_j L_j X L_j^dag (Schur-coordinate L~_j with schur=True)."""
+    Y = torch.empty_like(X) if Y is None else Y
+    st = load_library().jump_apply(h.ptr, _dev(X, (h.n, h.n)), _dev(Y, (h.n, h.n)), LB_APPLY_SCHUR if schur else 0,
+                                   precision, _stream())
+    if st != 0:
+        raise LindbladError(st, "jump_apply")
+    return Y
+
+
 def resolvent_apply(h: Handle, Y: torch.Tensor, lam: float, precision: int = LB_PREC_FP64) -> torch.Tensor:
     """X = (lam - S)^{-1}(Y)."""
     X = torch.empty_like(Y)
@@ -194,6 +213,26 @@ def low_spectrum(h: Handle, k: int, mu: float = 0.0, eta: float = 1.0, want_vect
     if st < 0:
         raise LindbladError(st, "low_spectrum")
     return ev, vecs, info.as_dict(), st
+
+
+def lb_set_profiling(h: Handle, enable: bool = True):
+    st = load_library().lb_set_profiling(h.ptr, 1 if enable else 0)
+    if st != 0:
+        raise LindbladError(st, "lb_set_profiling")
+
+
+def lb_kernel_stats(h: Handle, kernel: int = 0):
+    """(launches, total_ms, algorithmic_flops) of kernel id 0 (tensor-core GEMM) or 1 (FP64 GEMM)."""
+    n, ms, fl = ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
+    st = load_library().lb_kernel_stats(h.ptr, kernel, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(fl))
+    if st != 0:
+        raise LindbladError(st, "lb_kernel_stats")
+    return n.value, ms.value, fl.value
+
+
+def lb_launch_count() -> int:
+    """Kernels launched by the library in this process so far."""
+    return int(load_library().lb_launch_count())
 
 
 def lindblad_destroy(h: Handle):

@@ -28,7 +28,7 @@ def lib():
 
 def test_header_declares_the_boundary():
     names = _declared_functions()
-    for required in ("lindblad_setup", "phi_apply", "steady_state", "low_spectrum", "lindblad_destroy",
+    for required in ("lindblad_setup", "phi_apply", "jump_apply", "steady_state", "low_spectrum", "lindblad_destroy",
                      "lindblad_workspace_bytes", "resolvent_apply", "lindbladian_apply"):
         assert required in names
 
@@ -41,7 +41,7 @@ def test_every_declared_symbol_is_exported(lib):
 def test_opts_struct_layout_and_defaults(lib):
     from paper_2608_30860_b300 import lindblad as B
     o = B.default_opts()
-    assert o.tol == 1e-10 and o.krylov_m == 20 and o.eta == 1.0 and o.precision == B.LB_PREC_FP64
+    assert o.tol == 1e-10 and o.krylov_m == 20 and o.gmres_m == 40 and o.eta == 1.0 and o.precision == B.LB_PREC_FP64
     assert ctypes.sizeof(B.LbOpts) == 64   # C layout: 3 doubles, 7 ints, natural padding
     assert ctypes.sizeof(B.LbInfo) == 80
 
