@@ -156,7 +156,7 @@ lb_status steady_state(lindblad_handle h, void* rho_dev, const lb_opts* opts, lb
  *   evals_host : k complex128 (host memory), sorted by |lambda|, then Re descending.
  *   evecs_dev  : nullable; k stacked n x n device eigenvectors (raw, traceless).
  * Errors: LB_INVALID_ARG (k < 1 or k > m - 2), LB_ETA_EXCLUDED, LB_S_SINGULAR (mu = 0 with
- * S singular), LB_NOT_CONVERGED (best estimates returned). */
+ * S singular: no result is produced, choose mu > 0), LB_NOT_CONVERGED (best estimates returned). */
 lb_status low_spectrum(lindblad_handle h, int k, double mu, double eta, void* evals_host,
                        void* evecs_dev, const lb_opts* opts, lb_info* info, void* stream);
 

@@ -21,7 +21,8 @@
 constexpr int KMAX = 64;      // largest Krylov cycle (outer Arnoldi or inner GMRES)
 constexpr int NSCRATCH = 8;   // n x n scratch matrices
 
-struct MixedState;            // tensor-core path buffers (mixed.cu)
+struct MixedState;            // tensor-core jump-term buffers (mixed.cu)
+struct SylvMixed;             // tensor-core triangular Sylvester buffers (sylv_mixed.cu)
 
 struct lb_handle_s {
     int n = 0, d = 0;
@@ -51,6 +52,7 @@ struct lb_handle_s {
     size_t solver_ws_bytes = 0;
     char* mixed_base = nullptr;
     MixedState* mixed = nullptr;
+    SylvMixed* sylv = nullptr;
     bool mixed_ready = false;         // tensor-core jump term available
     bool mixed_sylv_ready = false;    // tensor-core triangular Sylvester available
     // host-side diagnostics
@@ -92,5 +94,10 @@ size_t mixed_bytes(int n, int d);
 size_t mixed_P_rows(int n, int d);
 int mixed_prepare(lb_handle_s* h, cudaStream_t s);
 int jump_mixed(lb_handle_s* h, cudaStream_t s, const cplx* Z, cplx* Y, double alpha);
-int trisylv_mixed(lb_handle_s* h, cudaStream_t s, cplx* X, double shift);
 void mixed_release(lb_handle_s* h);
+
+// sylv_mixed.cu
+size_t sylv_mixed_bytes(int n);
+int sylv_mixed_prepare(lb_handle_s* h, char* base, cudaStream_t s);
+int trisylv_mixed(lb_handle_s* h, cudaStream_t s, cplx* X, double shift);
+void sylv_mixed_release(lb_handle_s* h);

@@ -79,7 +79,7 @@ void layout(lb_handle_s* h, char* base, int n, int d, const lb_opts* o, size_t s
     h->ldh = KMAX + 1;
     h->hm = c.take<cplx>((size_t)(KMAX + 1) * (KMAX + 1));
     h->hm2 = c.take<cplx>((size_t)(KMAX + 1) * (KMAX + 1));
-    h->ev = c.take<cplx>(KMAX);
+    h->ev = c.take<cplx>(KMAX + 2);
     h->evec = c.take<cplx>((size_t)(KMAX + 2) * (KMAX + 2));
     h->small = c.take<cplx>(4 * (KMAX + 2));
     h->part = c.take<cplx>((size_t)DOT_BLOCKS * (KMAX + 2));
@@ -620,6 +620,7 @@ lb_status steady_state_arnoldi(lb_handle_s* h, cudaStream_t s, const lb_opts& o,
     if (mat_eye(h->V, n, cmake(1.0 / std::sqrt((double)n), 0.0), s)) return LB_CUDA_ERROR;
     OpFn op = [&](const cplx* x, cplx* y) { return phi_schur(h, s, x, y, 0, prec); };
     std::vector<cplx> evh(KMAX);
+    double prev_ritz = INFINITY;
     int restart = 0;
     for (; restart < o.max_restarts; ++restart) {
         int k = 0;
@@ -632,26 +633,45 @@ lb_status steady_state_arnoldi(lb_handle_s* h, cudaStream_t s, const lb_opts& o,
         for (int i = 0; i < k; ++i) th[i] = {evh[i].x, evh[i].y};
         const int idx = pick_nearest_one(th);
         inf->ritz_value = th[idx].real();
+        // Arnoldi residual estimate of the Ritz pair: |h_{k,k-1}| |y_{k-1}|
+        cplx tail[2];
+        LB_CHECK_CUDA(cudaMemcpyAsync(&tail[0], h->hm + (size_t)(k - 1) * h->ldh + k, sizeof(cplx),
+                                      cudaMemcpyDeviceToHost, s));
+        LB_CHECK_CUDA(cudaMemcpyAsync(&tail[1], h->evec + (size_t)idx * k + k - 1, sizeof(cplx),
+                                      cudaMemcpyDeviceToHost, s));
+        LB_CHECK_CUDA(cudaStreamSynchronize(s));
+        const double ritz_res = std::hypot(tail[0].x, tail[0].y) * std::hypot(tail[1].x, tail[1].y);
         // xi = V y, phase-fixed by its trace
         if (vec_gemv(xi, h->V, nn, k, h->evec + (size_t)idx * k, nn, 1.0, 0, s)) return LB_CUDA_ERROR;
         if (mat_trace(xi, n, h->scal + 2, s)) return LB_CUDA_ERROR;
         if (mat_div_by_dev(xi, xi, nn, h->scal + 2, s)) return LB_CUDA_ERROR;
-        // rho~ = -S~^{-1} xi, hermitised and trace-normalised
-        if (lyap_schur(h, s, xi, rt, 0.0, prec)) return LB_CUDA_ERROR;
-        if (hermitize_normalize(h, s, rt, rt, R)) return LB_CUDA_ERROR;
-        if (change_basis(h, s, rt, rho, R, 0)) return LB_CUDA_ERROR;
-        // the returned state is hermitised and trace-normalised in the original basis
-        if (hermitize_normalize(h, s, rho, rho, R)) return LB_CUDA_ERROR;
-        double rmax, rfro;
-        if (residual_norms(h, s, rho, R, &rmax, &rfro)) return LB_CUDA_ERROR;
-        if (rmax < best) {
-            best = rmax;
-            inf->residual_max = rmax;
-            inf->residual_fro = rfro;
-            LB_CHECK_CUDA(cudaMemcpyAsync(rho_out, rho, nn * sizeof(cplx), cudaMemcpyDeviceToDevice, s));
-            LB_CHECK_CUDA(cudaMemcpyAsync(h->best, rt, nn * sizeof(cplx), cudaMemcpyDeviceToDevice, s));
+        bool reconstruct = true;
+        if (prec == LB_PREC_MIXED) {
+            // low-precision phase: iterate until the Ritz residual reaches the split-GEMM accuracy
+            // floor or stops halving; the state is then reconstructed once and refined in FP64
+            const bool stop = ritz_res < 1e-7 * std::abs(th[idx]) || (restart > 0 && ritz_res > 0.5 * prev_ritz) ||
+                              restart + 1 == o.max_restarts;
+            prev_ritz = std::min(prev_ritz, ritz_res);
+            reconstruct = stop;
         }
-        if (rmax < o.tol) { ++restart; break; }
+        if (reconstruct) {
+            // rho~ = -S~^{-1} xi, hermitised and trace-normalised
+            if (lyap_schur(h, s, xi, rt, 0.0, prec)) return LB_CUDA_ERROR;
+            if (hermitize_normalize(h, s, rt, rt, R)) return LB_CUDA_ERROR;
+            if (change_basis(h, s, rt, rho, R, 0)) return LB_CUDA_ERROR;
+            // the returned state is hermitised and trace-normalised in the original basis
+            if (hermitize_normalize(h, s, rho, rho, R)) return LB_CUDA_ERROR;
+            double rmax, rfro;
+            if (residual_norms(h, s, rho, R, &rmax, &rfro)) return LB_CUDA_ERROR;
+            if (rmax < best) {
+                best = rmax;
+                inf->residual_max = rmax;
+                inf->residual_fro = rfro;
+                LB_CHECK_CUDA(cudaMemcpyAsync(rho_out, rho, nn * sizeof(cplx), cudaMemcpyDeviceToDevice, s));
+                LB_CHECK_CUDA(cudaMemcpyAsync(h->best, rt, nn * sizeof(cplx), cudaMemcpyDeviceToDevice, s));
+            }
+            if (rmax < o.tol || prec == LB_PREC_MIXED) { ++restart; break; }
+        }
         // restart from xi (unit norm)
         if (vec_norms(xi, nn, h->dpart, h->dscal, s)) return LB_CUDA_ERROR;
         double nr[2];

@@ -33,7 +33,7 @@ __global__ void k_mul2(double* out, const double* a, const double* b) {
 size_t mixed_bytes(int n, int d) {
     const size_t np = (size_t)round_up(n, tc::BM);
     const size_t planes1 = 4 * np * np * sizeof(__half);
-    return (size_t)d * planes1 + planes1 + (size_t)d * planes1 + 64 * sizeof(double) + 3 * 256;
+    return (size_t)d * planes1 + planes1 + (size_t)d * planes1 + 64 * sizeof(double) + 4 * 256 + sylv_mixed_bytes(n);
 }
 
 size_t mixed_P_rows(int n, int d) { return (size_t)d * round_up(n, tc::BM); }
@@ -65,7 +65,7 @@ int mixed_prepare(lb_handle_s* h, cudaStream_t s) {
     if (tc_make_map(&m->maps.m[2], m->Pp, (int)np, (int)np, d, (int)np)) return -1;
     if (tc_make_map(&m->maps.m[3], m->Lp, (int)np, (int)np, d, (int)np)) return -1;
     h->mixed_ready = true;
-    return 0;
+    return sylv_mixed_prepare(h, base, s);
 }
 
 // Y = alpha * sum_j L~_j Z L~_j^dag  (Z, Y: n x n complex128, Schur coordinates)
@@ -93,6 +93,8 @@ int jump_mixed(lb_handle_s* h, cudaStream_t s, const cplx* Z, cplx* Y, double al
     p1.scale = m->sc + 6;
     p1.accumulate = 0;
     p1.err = err;
+    p1.fmt = 0;
+    p1.wave = -1;
     prof_begin(h, s, 0);
     if (tc_gemm_launch(m->maps, p1, d * np / tc::BM, (n + tc::BN - 1) / tc::BN, s)) return -1;
     prof_end(h, s, 0, 8.0 * d * (double)n * n * n);
@@ -116,17 +118,18 @@ int jump_mixed(lb_handle_s* h, cudaStream_t s, const cplx* Z, cplx* Y, double al
     p2.scale = m->sc + 7;
     p2.accumulate = 0;
     p2.err = err;
+    p2.fmt = 0;
+    p2.wave = -1;
     prof_begin(h, s, 0);
     const int r = tc_gemm_launch(m->maps, p2, (n + tc::BM - 1) / tc::BM, (n + tc::BN - 1) / tc::BN, s);
     prof_end(h, s, 0, 8.0 * d * (double)n * n * n);
     return r;
 }
 
-int trisylv_mixed(lb_handle_s*, cudaStream_t, cplx*, double) { return -1; }
-
 void mixed_release(lb_handle_s* h) {
     delete h->mixed;
     h->mixed = nullptr;
+    sylv_mixed_release(h);
 }
 
 lb_handle_s::~lb_handle_s() { mixed_release(this); }

@@ -205,42 +205,60 @@ static int shifted_deflated_apply(lb_handle_s* h, cudaStream_t s, const cplx* X,
     return mat_add_diag_dev(out, n, h->scal + 10, -eta, s);
 }
 
-// Restarted right-preconditioned GMRES(m) for (mu - L~_eta) x = b in Schur coordinates,
-// preconditioner Precond(., mu, eta).  x holds the initial guess.  Stops when the true
-// residual norm <= atol or after max_cycles.  Uses V / hm (inner basis), X[5], X[6], X[7].
+// residual coefficients after a GMRES cycle: g = beta e1 - Hbar y ((k+1)-vector), so that the new
+// residual is V_{k+1} g (Arnoldi relation A P V_k = V_{k+1} Hbar)
+__global__ void k_gmres_resid_coeffs(const cplx* Hb, int ldh, int k, double beta, const cplx* y, cplx* g) {
+    for (int i = threadIdx.x; i <= k; i += blockDim.x) {
+        cplx acc = cmake(i == 0 ? beta : 0.0, 0.0);
+        for (int j = (i > 0 ? i - 1 : 0); j < k; ++j) acc = csub(acc, cmul(Hb[(long long)j * ldh + i], y[j]));
+        g[i] = acc;
+    }
+}
+
+// Restarted right-preconditioned GMRES(m) for (mu - L~_eta) x = b in Schur coordinates, from
+// x = 0, preconditioner P = Precond(., mu, eta).  Because P inverts (mu - S~) - eta |I><I| exactly
+// (Sherman-Morrison), the preconditioned operator is (mu - L~_eta) P = Id - K~ P (the right-
+// preconditioning identity of Sec. 3.1): one Lyapunov solve and one jump term per step, no
+// application of S~.  Residuals between cycles follow from the Arnoldi relation.  Stops when the
+// residual norm <= atol, on stagnation (< 10% gain per cycle) or after max_cycles.
+// Uses V / hm (inner basis), X[5], X[6], X[7].
 static int gmres_solve(lb_handle_s* h, cudaStream_t s, const cplx* b, cplx* x, double mu, double eta, int m,
                        int max_cycles, double atol, int precision, int* steps, double* final_res) {
     const long long nn = (long long)h->n * h->n;
-    cplx* r = h->V;
-    cplx* tmp = h->X[5];
+    cplx* r = h->X[5];
     cplx* pv = h->X[6];
     cplx* y = h->small + 3 * (KMAX + 2);
+    cplx* g = h->ev;   // (k+1) residual coefficients
     double* dres = h->dscal + 6;
     OpFn op = [&](const cplx* v, cplx* w) {
-        // (mu - L~_eta) P v = v - K~(P v)  by the right-preconditioning identity (Sec. 3.1);
-        // evaluated explicitly so that an inexact inner solve is still measured honestly
         if (precond_apply(h, s, v, pv, mu, eta, precision)) return -1;
-        return shifted_deflated_apply(h, s, pv, w, mu, eta, precision);
+        if (precision == LB_PREC_MIXED && h->mixed_ready) {
+            if (jump_mixed(h, s, pv, w, -1.0)) return -1;
+        } else if (jump_f64(h, s, h->Lt, pv, w, cmake(-1, 0), cmake(0, 0))) {
+            return -1;
+        }
+        return vec_axpby(w, v, nn, cmake(1, 0), cmake(1, 0), s);
     };
-    double res = INFINITY;
-    for (int cyc = 0; cyc < max_cycles; ++cyc) {
-        if (shifted_deflated_apply(h, s, x, tmp, mu, eta, precision)) return -1;
-        if (vec_scale_copy(r, b, nn, cmake(1, 0), s)) return -1;
-        if (vec_axpby(r, tmp, nn, cmake(-1, 0), cmake(1, 0), s)) return -1;
-        if (vec_norms(r, nn, h->dpart, h->dscal, s)) return -1;
-        double beta = read_double(s, h->dscal + 1);
-        const double prev = res;
-        res = beta;
-        if (!(beta > atol)) break;
-        if (cyc > 0 && beta > 0.9 * prev) break;   // stagnation: a cycle gained less than 10%
-        if (vec_scale_copy(r, r, nn, cmake(1.0 / beta, 0), s)) return -1;
+    if (vec_scale_copy(x, b, nn, cmake(0, 0), s)) return -1;
+    if (vec_scale_copy(r, b, nn, cmake(1, 0), s)) return -1;
+    if (vec_norms(r, nn, h->dpart, h->dscal, s)) return -1;
+    double beta = read_double(s, h->dscal + 1);
+    double res = beta;
+    for (int cyc = 0; cyc < max_cycles && beta > atol; ++cyc) {
+        if (vec_scale_copy(h->V, r, nn, cmake(1.0 / beta, 0), s)) return -1;
         int k = 0;
         if (arnoldi_cycle(h, s, h->V, h->hm, 0, m, op, &k)) return -1;
         *steps += k;
         k_hess_lstsq<<<1, 32, 0, s>>>(h->hm, h->ldh, k, beta, h->evec, y, dres); lb_note_launch();
-        if (vec_gemv(tmp, h->V, nn, k, y, nn, 1.0, 0, s)) return -1;      // u = V y
-        if (precond_apply(h, s, tmp, pv, mu, eta, precision)) return -1;   // P u
-        if (vec_axpby(x, pv, nn, cmake(1, 0), cmake(1, 0), s)) return -1;
+        if (vec_gemv(r, h->V, nn, k, y, nn, 1.0, 0, s)) return -1;           // u = V y
+        if (precond_apply(h, s, r, pv, mu, eta, precision)) return -1;     // P u
+        if (vec_axpby(x, pv, nn, cmake(1, 0), cmake(1, 0), s)) return -1;  // x += P u
+        k_gmres_resid_coeffs<<<1, 64, 0, s>>>(h->hm, h->ldh, k, beta, y, g); lb_note_launch();
+        if (vec_gemv(r, h->V, nn, k + 1, g, nn, 1.0, 0, s)) return -1;      // r = V_{k+1} g
+        const double prev = beta;
+        beta = read_double(s, dres);
+        res = beta;
+        if (beta > 0.9 * prev) break;   // stagnation
     }
     *final_res = res;
     return 0;
@@ -316,6 +334,8 @@ extern "C" lb_status low_spectrum(lindblad_handle h, int k, double mu, double et
     inf.setup_ms = h->setup_ms;
     lb_status st = precond_prepare(h, s, mu, eta, o.precision);
     if (st != LB_OK) return st;
+    // the outer relation matrix is read as a general matrix by the small Schur kernel: clear it
+    LB_CHECK_CUDA(cudaMemsetAsync(h->hm2, 0, (size_t)(KMAX + 1) * (KMAX + 1) * sizeof(cplx), s));
     // start vector: traceless, unit norm
     cplx* Zb = h->Z;
     k_start_vector<<<grid1(nn), 256, 0, s>>>(Zb, n, 12345u); lb_note_launch();

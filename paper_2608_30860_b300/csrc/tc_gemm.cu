@@ -10,6 +10,7 @@
 // Three-stage ring.  Every mbarrier wait is bounded (~2 s of %globaltimer); a timeout sets the
 // error word and the roles fall through to the TMEM release.
 #include <cuda.h>
+#include <cuda_bf16.h>
 
 #include "tc_gemm.cuh"
 
@@ -108,7 +109,18 @@ constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)
 constexpr uint32_t NEG_A = 1u << 13;
 
 __device__ __forceinline__ int seg_iters(const Seg& sg, int npairs) {
-    return sg.nbatch * ((sg.klen + BK - 1) / BK) * npairs;
+    return sg.klen > 0 ? sg.nbatch * ((sg.klen + BK - 1) / BK) * npairs : 0;
+}
+
+// segment g of this CTA (wavefront mode adjusts the K ranges to the block (I, J))
+__device__ __forceinline__ Seg cta_seg(const Params& p, int g, int I, int J) {
+    Seg sg = p.seg[g];
+    if (p.wave >= 0) {
+        const int lo = (g == 0 ? I + 1 : J + 1) * BM;
+        sg.k0 = lo;
+        sg.klen = p.nb * BM - lo;
+    }
+    return sg;
 }
 
 __global__ void __launch_bounds__(256, 1) k_tc_gemm(const __grid_constant__ Maps maps,
@@ -125,7 +137,17 @@ __global__ void __launch_bounds__(256, 1) k_tc_gemm(const __grid_constant__ Maps
     const uint32_t accf = full0 + 16 * STAGES;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN, I = 0, J = 0;
+    if (p.wave >= 0) {
+        const int t = blockIdx.x + max(0, p.wave - (p.nb - 1));
+        I = p.nb - 1 - t;
+        J = p.nb - 1 - (p.wave - t);
+        m0 = I * BM;
+        n0 = J * BN;
+    }
+    int total_iters = 0;
+    for (int g = 0; g < p.nseg; ++g) total_iters += seg_iters(cta_seg(p, g, I, J), p.npairs);
+    const uint32_t idesc_base = IDESC | ((uint32_t)p.fmt << 7) | ((uint32_t)p.fmt << 10);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -151,7 +173,8 @@ __global__ void __launch_bounds__(256, 1) k_tc_gemm(const __grid_constant__ Maps
         int it = 0;
         bool ok = true;
         for (int g = 0; g < p.nseg && ok; ++g) {
-            const Seg& sg = p.seg[g];
+            const Seg sg = cta_seg(p, g, I, J);
+            if (sg.klen <= 0) continue;
             const int nkb = (sg.klen + BK - 1) / BK;
             const CUtensorMap* am = &maps.m[sg.a_map];
             const CUtensorMap* bm = &maps.m[sg.b_map];
@@ -183,10 +206,11 @@ __global__ void __launch_bounds__(256, 1) k_tc_gemm(const __grid_constant__ Maps
         int it = 0;
         bool ok = true;
         for (int g = 0; g < p.nseg && ok; ++g) {
-            const Seg& sg = p.seg[g];
-            const uint32_t id_ii = (sg.sign == SIGN_NORMAL) ? (IDESC | NEG_A) : IDESC;
-            const uint32_t id_ri = (sg.sign == SIGN_CONJ_B) ? (IDESC | NEG_A) : IDESC;
-            const uint32_t id_ir = (sg.sign == SIGN_CONJ_A) ? (IDESC | NEG_A) : IDESC;
+            const Seg sg = cta_seg(p, g, I, J);
+            const uint32_t id_rr = idesc_base;
+            const uint32_t id_ii = (sg.sign == SIGN_NORMAL) ? (idesc_base | NEG_A) : idesc_base;
+            const uint32_t id_ri = (sg.sign == SIGN_CONJ_B) ? (idesc_base | NEG_A) : idesc_base;
+            const uint32_t id_ir = (sg.sign == SIGN_CONJ_A) ? (idesc_base | NEG_A) : idesc_base;
             const int n_it = seg_iters(sg, p.npairs);
             for (int q = 0; q < n_it; ++q, ++it) {
                 const int s = it % STAGES;
@@ -200,7 +224,7 @@ __global__ void __launch_bounds__(256, 1) k_tc_gemm(const __grid_constant__ Maps
                 for (int t = 0; t < BK / 16; ++t) {
                     const uint64_t off = (uint64_t)((t * 32) >> 4);   // 16 fp16 = 32 bytes along K
                     const uint32_t acc = (it == 0 && t == 0) ? 0u : 1u;
-                    umma(tmem, dAr + off, dBr + off, IDESC, acc);
+                    umma(tmem, dAr + off, dBr + off, id_rr, acc);
                     umma(tmem, dAi + off, dBi + off, id_ii, 1u);
                     umma(tmem + BN, dAr + off, dBi + off, id_ri, acc);
                     umma(tmem + BN, dAi + off, dBr + off, id_ir, 1u);
@@ -208,8 +232,8 @@ __global__ void __launch_bounds__(256, 1) k_tc_gemm(const __grid_constant__ Maps
                 umma_commit(empty0 + 8 * s);
             }
         }
-        umma_commit(accf);
-    } else if (warp >= 4) {
+        if (total_iters > 0) umma_commit(accf);
+    } else if (warp >= 4 && total_iters > 0) {
         // ---------------------------------------------------------------- epilogue
         const int wq = warp - 4;
         const bool ok = mbar_wait(accf, 0, p.err, 3);
@@ -286,6 +310,36 @@ __global__ void k_split_planes(const cplx* __restrict__ X, long long ld_src, int
     }
 }
 
+// BF16 hi/lo planes, no scale (8-bit exponent): hi = bf16(v), lo = bf16(v - hi)
+__global__ void k_split_planes_bf16(const cplx* __restrict__ X, long long ld_src, int rows, int cols, int transpose,
+                                    __nv_bfloat16* __restrict__ planes, int ld_dst, int rows_pad, long long pstride) {
+    __shared__ cplx tile[32][33];
+    const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+    for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
+        if (transpose) {
+            const int k = k0 + yy, r = r0 + threadIdx.x;
+            tile[yy][threadIdx.x] = (k < cols && r < rows) ? X[(long long)k * ld_src + r] : cmake(0, 0);
+        } else {
+            const int r = r0 + yy, k = k0 + threadIdx.x;
+            tile[yy][threadIdx.x] = (r < rows && k < cols) ? X[(long long)r * ld_src + k] : cmake(0, 0);
+        }
+    }
+    __syncthreads();
+    for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
+        const int r = r0 + yy, k = k0 + threadIdx.x;
+        if (r >= rows_pad || k >= ld_dst) continue;
+        const cplx v = transpose ? tile[threadIdx.x][yy] : tile[yy][threadIdx.x];
+        const __nv_bfloat16 rh = __double2bfloat16(v.x), ih = __double2bfloat16(v.y);
+        const __nv_bfloat16 rl = __double2bfloat16(v.x - (double)__bfloat162float(rh));
+        const __nv_bfloat16 il = __double2bfloat16(v.y - (double)__bfloat162float(ih));
+        const long long o = (long long)r * ld_dst + k;
+        planes[o] = rh;
+        planes[pstride + o] = rl;
+        planes[2 * pstride + o] = ih;
+        planes[3 * pstride + o] = il;
+    }
+}
+
 // power-of-two scale with scale * maxabs <= 2^14
 __global__ void k_pick_scale(const double* maxabs, double* scale, double* inv) {
     if (threadIdx.x != 0) return;
@@ -319,14 +373,15 @@ EncodeTiledFn encode_fn() {
 }  // namespace
 }  // namespace tc
 
-int tc_make_map(CUtensorMap* map, const __half* planes, int K, int rows, int nbatch, int ld) {
+int tc_make_map(CUtensorMap* map, const void* planes, int K, int rows, int nbatch, int ld, int bf16) {
     tc::EncodeTiledFn fn = tc::encode_fn();
     if (!fn || (ld % 8) != 0 || (reinterpret_cast<uintptr_t>(planes) & 15) != 0) return -1;
     cuuint64_t dims[4] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)nbatch, 4};
     cuuint64_t strides[3] = {(cuuint64_t)ld * 2, (cuuint64_t)rows * ld * 2, (cuuint64_t)nbatch * rows * ld * 2};
     cuuint32_t box[4] = {tc::BK, tc::BM, 1, 1};
     cuuint32_t estr[4] = {1, 1, 1, 1};
-    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, const_cast<__half*>(planes), dims, strides, box, estr,
+    CUresult r = fn(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4,
+                    const_cast<void*>(planes), dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? 0 : -1;
@@ -341,8 +396,9 @@ int tc_gemm_launch(const tc::Maps& maps, const tc::Params& p, int grid_m, int gr
         attr = true;
     }
     if (grid_m <= 0 || grid_n <= 0 || p.nseg < 1 || p.nseg > tc::MAX_SEGS) return -1;
-    for (int g = 0; g < p.nseg; ++g)
-        if (p.seg[g].nbatch < 1 || p.seg[g].klen < 1) return -1;
+    if (p.wave < 0)
+        for (int g = 0; g < p.nseg; ++g)
+            if (p.seg[g].nbatch < 1 || p.seg[g].klen < 1) return -1;
     tc::k_tc_gemm<<<dim3(grid_m, grid_n), 256, tc::SMEM_BYTES, s>>>(maps, p); lb_note_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
@@ -355,6 +411,16 @@ int tc_split_planes(const cplx* X, long long ld_src, int rows, int cols, int tra
     dim3 grid((ld_dst + 31) / 32, (rows_pad + 31) / 32, batch);
     tc::k_split_planes<<<grid, dim3(32, 8), 0, s>>>(X, ld_src, rows, cols, transpose, conj, scale_dev, planes,
                                                      ld_dst, rows_pad, pstride, src_bstride, dst_bstride); lb_note_launch();
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int tc_split_planes_bf16(const cplx* X, long long ld_src, int rows, int cols, int transpose, void* planes,
+                         int ld_dst, long long pstride, cudaStream_t s) {
+    const int rows_pad = (int)(pstride / ld_dst);
+    dim3 grid((ld_dst + 31) / 32, (rows_pad + 31) / 32, 1);
+    tc::k_split_planes_bf16<<<grid, dim3(32, 8), 0, s>>>(X, ld_src, rows, cols, transpose,
+                                                          reinterpret_cast<__nv_bfloat16*>(planes), ld_dst, rows_pad,
+                                                          pstride); lb_note_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

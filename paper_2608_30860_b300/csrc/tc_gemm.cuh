@@ -53,18 +53,27 @@ struct Params {
     const double* scale;     // device scalar (product of the operands' inverse scales), nullable
     int accumulate;          // 1: out += result
     int* err;                // device error word (set on a wait timeout)
+    int fmt;                 // operand format: 0 FP16, 1 BF16
+    // wavefront mode (triangular Sylvester updates): wave >= 0 maps CTA b to the block
+    // (I, J) = (nb-1-t, nb-1-(wave-t)), t = b + max(0, wave-(nb-1)); segment 0 then runs
+    // over K in [(I+1) BM, nb BM) and segment 1 over [(J+1) BN, nb BN)
+    int wave;
+    int nb;
 };
 
 }  // namespace tc
 
 // host-side helpers (tc_gemm.cu)
 // planes: 4 * nbatch * rows * ld halves, plane-major; builds a 4D map (K, rows, nbatch, 4)
-int tc_make_map(CUtensorMap* map, const __half* planes, int K, int rows, int nbatch, int ld);
+int tc_make_map(CUtensorMap* map, const void* planes, int K, int rows, int nbatch, int ld, int bf16 = 0);
 int tc_gemm_launch(const tc::Maps& maps, const tc::Params& p, int grid_m, int grid_n, cudaStream_t s);
 // X (complex128, rows x cols, ld_src) -> 4 FP16 planes (rows x ld_dst, plane stride pstride),
 // element op: transpose (op = 1) / conjugate (conj = 1); value scaled by scale_dev[0].
 int tc_split_planes(const cplx* X, long long ld_src, int rows, int cols, int transpose, int conj,
                     const double* scale_dev, __half* planes, int ld_dst, long long pstride, int batch,
                     long long src_bstride, long long dst_bstride, cudaStream_t s);
+// the same packing into BF16 hi/lo planes, no scale
+int tc_split_planes_bf16(const cplx* X, long long ld_src, int rows, int cols, int transpose, void* planes,
+                         int ld_dst, long long pstride, cudaStream_t s);
 // scale_dev[0] = 2^e with 2^e * maxabs <= 2^14 ; inv_dev[0] = 2^-e  (maxabs from vec_norms)
 int tc_pick_scale(const double* maxabs_dev, double* scale_dev, double* inv_dev, cudaStream_t s);

@@ -210,7 +210,7 @@ def low_spectrum(h: Handle, k: int, mu: float = 0.0, eta: float = 1.0, want_vect
     st = load_library().low_spectrum(h.ptr, k, float(mu), float(eta), ev.data_ptr(),
                                      None if vecs is None else vecs.data_ptr(), ctypes.byref(o),
                                      ctypes.byref(info), _stream())
-    if st < 0:
+    if st < 0 or st == 2:   # LB_S_SINGULAR: mu = 0 with S singular produces no spectrum
         raise LindbladError(st, "low_spectrum")
     return ev, vecs, info.as_dict(), st
 
