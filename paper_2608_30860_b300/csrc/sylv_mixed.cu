@@ -7,10 +7,9 @@
 //         C_IJ -= sum_{K>I} T_IK X_KJ + sum_{L>J} X_IL T_JL^dag,
 //       one tcgen05 CTA per block (tc_gemm.cu, wavefront mode, BF16 hi/lo operands -- BF16 keeps
 //       FP32's exponent range, so the unknown magnitude of X needs no scale);
-//   (2) the leaf solve of each block in FP32 on the CUDA cores, itself a wavefront over 4 x 4
-//       sub-blocks of 32 x 32 whose 32 x 32 leaves are eliminated diagonal by diagonal.  The
-//       leaf writes X_IJ back (complex128) and refreshes the BF16 planes of X and X^T that the
-//       later updates read.
+//   (2) the leaf solve of each block in FP32 on the CUDA cores: a left-looking sweep over the
+//       block's 255 anti-diagonals (4 threads per entry).  The leaf writes X_IJ back (complex128)
+//       and refreshes the BF16 planes of X and X^T that the later updates read.
 #include <cuda_bf16.h>
 
 #include "lb_internal.cuh"
@@ -22,116 +21,118 @@ struct SylvMixed {
     __nv_bfloat16* Tp = nullptr;    // 4 x np x np, rows of T (unshifted)
     __nv_bfloat16* Xp = nullptr;    // 4 x np x np, rows of X
     __nv_bfloat16* XTp = nullptr;   // 4 x np x np, rows of X^T
+    float2* Tf = nullptr;           // np x np, T in FP32 (row-major)
+    float2* Ttf = nullptr;          // np x np, T^T in FP32
     tc::Maps maps{};                // 0: T, 1: X^T, 2: X
 };
 
 namespace {
 
 constexpr int LB = 128;   // wavefront block
-constexpr int SB = 32;    // leaf sub-block
-constexpr int LEAF_THREADS = 256;
-// shared-memory row pitch in complex floats: 130 * 8 B = 1040 B, so that the anti-diagonal
-// accesses X[p0 + S - b][q0 + b] of the leaf sweep (stride -pitch + 8 B across lanes) spread over
-// the banks (a pitch of 129 would put all 32 lanes on one bank)
-constexpr int PITCH = LB + 2;
+constexpr int LEAF_THREADS = 512;   // 4 threads per entry of an anti-diagonal (<= 128 entries)
+// shared-memory row pitch in complex floats.  A warp holds 8 anti-diagonal entries (slot s,
+// a = a0 + s, b = S - a) x 4 threads t; its loads X[a+1+t][b] and X[a][b+1+t] sit at word offsets
+// (pitch-1) s + pitch t and (pitch-1) s + t.  With pitch = 5 (mod 32) both sets cover the 32
+// eight-byte bank pairs exactly once.
+constexpr int PITCH = LB + 5;
 
 struct f2 {
     float x, y;
 };
 __device__ __forceinline__ f2 fmk(float a, float b) { return f2{a, b}; }
 
+__device__ __forceinline__ f2 f2ld(const float2* p) { const float2 v = __ldg(p); return fmk(v.x, v.y); }
+
+// Leaf of one 128 x 128 block (I, J) of the wavefront: A X + X B^dag = C with A = T_II - sI,
+// B = T_JJ - sI (upper triangular), C already updated by the tensor-core step.  Left-looking
+// anti-diagonal sweep over the whole block: the entries (a, b) with a + b = S are independent and
+//   X_ab = (C_ab - sum_{r>a} A_ar X_rb - sum_{r>b} X_ar conj(B_br)) / (A_aa + conj(B_bb)),
+// each dot product of the same length 254 - S, split over 4 threads and reduced by shuffles.
+// A is kept in shared memory as a packed upper triangle; B rows are read through L1/L2.
 __global__ void __launch_bounds__(LEAF_THREADS, 1)
-k_sylv_leaf128(const cplx* __restrict__ T, cplx* __restrict__ X, int n, double sh, int wave, int nb,
-               __nv_bfloat16* __restrict__ Xp, __nv_bfloat16* __restrict__ XTp, int np) {
+k_sylv_leaf128(const float2* __restrict__ Tf, const float2* __restrict__ Ttf, int ldf, cplx* __restrict__ X, int n,
+               float sh, int wave, int nb, __nv_bfloat16* __restrict__ Xp, __nv_bfloat16* __restrict__ XTp,
+               int np) {
     extern __shared__ __align__(16) unsigned char smraw[];
     f2(*Xs)[PITCH] = reinterpret_cast<f2(*)[PITCH]>(smraw);                       // 128 x PITCH
-    f2(*Ta)[PITCH] = reinterpret_cast<f2(*)[PITCH]>(smraw + sizeof(f2) * LB * PITCH);
-    f2(*Tb)[PITCH] = Ta + SB;                                                     // 32 x PITCH each
+    f2* Ap = reinterpret_cast<f2*>(smraw + sizeof(f2) * LB * PITCH);              // packed upper triangle
     const int t = blockIdx.x + max(0, wave - (nb - 1));
     const int I = nb - 1 - t, J = nb - 1 - (wave - t);
     const int r0 = I * LB, c0 = J * LB;
     const int br = min(LB, n - r0), bc = min(LB, n - c0);
     const int tid = threadIdx.x;
-    const float s = (float)sh;
+    (void)Ttf;
 
     for (int e = tid; e < LB * LB; e += LEAF_THREADS) {
         const int p = e / LB, q = e % LB;
         cplx v = (p < br && q < bc) ? X[(long long)(r0 + p) * n + c0 + q] : cmake(0, 0);
         Xs[p][q] = fmk((float)v.x, (float)v.y);
+        if (q >= p) {
+            f2 a = (p < br && q < br) ? f2ld(Tf + (long long)(r0 + p) * ldf + r0 + q) : fmk(0.f, 0.f);
+            if (q == p) a.x -= sh;
+            Ap[p * LB - (p * (p - 1)) / 2 + (q - p)] = a;
+        }
     }
     __syncthreads();
 
-    const int PB = (br + SB - 1) / SB, QB = (bc + SB - 1) / SB;
-    for (int sw = 0; sw <= (PB - 1) + (QB - 1); ++sw) {
-        for (int P = PB - 1; P >= 0; --P) {
-            const int Q = (PB - 1 - P) + (QB - 1) - sw;   // (PB-1-P) + (QB-1-Q) = sw
-            if (Q < 0 || Q >= QB) continue;
-            const int p0 = P * SB, q0 = Q * SB;
-            const int sp = min(SB, br - p0), sq = min(SB, bc - q0);
-            // stage rows p0.. of A = T_II - sI and rows q0.. of B = T_JJ - sI (columns >= block start)
-            for (int e = tid; e < SB * LB; e += LEAF_THREADS) {
-                const int a = e / LB, k = e % LB;
-                cplx va = (a < sp && k >= p0 && k < br) ? T[(long long)(r0 + p0 + a) * n + r0 + k] : cmake(0, 0);
-                cplx vb = (a < sq && k >= q0 && k < bc) ? T[(long long)(c0 + q0 + a) * n + c0 + k] : cmake(0, 0);
-                if (k == p0 + a) va.x -= sh;
-                if (k == q0 + a) vb.x -= sh;
-                Ta[a][k] = fmk((float)va.x, (float)va.y);
-                Tb[a][k] = fmk((float)vb.x, (float)vb.y);
+    const int slot = tid >> 2, t4 = tid & 3;
+    for (int S = (br - 1) + (bc - 1); S >= 0; --S) {
+        const int a = max(0, S - (bc - 1)) + slot;
+        const int b = S - a;
+        const bool valid = a < br && b >= 0 && a <= S;
+        f2 acc = fmk(0.f, 0.f);
+        if (valid) {
+            // four independent partial sums so that four loads are in flight
+            f2 p[4] = {fmk(0.f, 0.f), fmk(0.f, 0.f), fmk(0.f, 0.f), fmk(0.f, 0.f)};
+            const int arow = a * LB - (a * (a - 1)) / 2 - a;      // Ap index of A[a][r] = arow + r
+            int r = a + 1 + t4;
+            for (; r + 12 < br; r += 16) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const f2 m = Ap[arow + r + 4 * u], x = Xs[r + 4 * u][b];
+                    p[u].x += m.x * x.x - m.y * x.y;
+                    p[u].y += m.x * x.y + m.y * x.x;
+                }
             }
-            __syncthreads();
-            // update from the solved sub-blocks below (rows > p0+32) and to the right (cols > q0+32)
-            for (int e = tid; e < SB * SB; e += LEAF_THREADS) {
-                const int a = e / SB, b = e % SB;
-                if (a >= sp || b >= sq) continue;
-                f2 acc = Xs[p0 + a][q0 + b];
-                for (int k = p0 + SB; k < br; ++k) {
-                    const f2 m = Ta[a][k], x = Xs[k][q0 + b];
-                    acc.x -= m.x * x.x - m.y * x.y;
-                    acc.y -= m.x * x.y + m.y * x.x;
-                }
-                for (int k = q0 + SB; k < bc; ++k) {
-                    const f2 x = Xs[p0 + a][k], m = Tb[b][k];   // X[a][k] conj(B[b][k])
-                    acc.x -= x.x * m.x + x.y * m.y;
-                    acc.y -= x.y * m.x - x.x * m.y;
-                }
-                Xs[p0 + a][q0 + b] = acc;
+            for (; r < br; r += 4) {
+                const f2 m = Ap[arow + r], x = Xs[r][b];
+                p[0].x += m.x * x.x - m.y * x.y;
+                p[0].y += m.x * x.y + m.y * x.x;
             }
-            __syncthreads();
-            // 32 x 32 leaf: A_s X + X B_s^dag = acc, diagonals p + q = S from the corner
-            for (int S = (sp - 1) + (sq - 1); S >= 0; --S) {
-                for (int e = tid; e < SB * SB; e += LEAF_THREADS) {
-                    const int a = e / SB, b = e % SB;
-                    if (a < sp && b < sq && a + b == S) {
-                        const f2 da = Ta[a][p0 + a], db = Tb[b][q0 + b];
-                        const float dr = da.x + db.x, di = da.y - db.y;   // A_aa + conj(B_bb)
-                        const float inv = 1.0f / (dr * dr + di * di);
-                        const f2 v = Xs[p0 + a][q0 + b];
-                        Xs[p0 + a][q0 + b] = fmk((v.x * dr + v.y * di) * inv, (v.y * dr - v.x * di) * inv);
-                    }
+            const float2* brow = Tf + (long long)(c0 + b) * ldf + c0;
+            r = b + 1 + t4;
+            for (; r + 12 < bc; r += 16) {
+                f2 m[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) m[u] = f2ld(brow + r + 4 * u);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const f2 x = Xs[a][r + 4 * u];
+                    p[u].x += x.x * m[u].x + x.y * m[u].y;
+                    p[u].y += x.y * m[u].x - x.x * m[u].y;
                 }
-                __syncthreads();
-                for (int e = tid; e < SB * SB; e += LEAF_THREADS) {
-                    const int a = e / SB, b = e % SB;
-                    if (a < sp && b < sq && a + b < S) {
-                        f2 v = Xs[p0 + a][q0 + b];
-                        int r = S - b;
-                        if (r < sp) {
-                            const f2 m = Ta[a][p0 + r], x = Xs[p0 + r][q0 + b];
-                            v.x -= m.x * x.x - m.y * x.y;
-                            v.y -= m.x * x.y + m.y * x.x;
-                        }
-                        r = S - a;
-                        if (r < sq) {
-                            const f2 x = Xs[p0 + a][q0 + r], m = Tb[b][q0 + r];
-                            v.x -= x.x * m.x + x.y * m.y;
-                            v.y -= x.y * m.x - x.x * m.y;
-                        }
-                        Xs[p0 + a][q0 + b] = v;
-                    }
-                }
-                __syncthreads();
             }
+            for (; r < bc; r += 4) {
+                const f2 x = Xs[a][r], m = f2ld(brow + r);
+                p[1].x += x.x * m.x + x.y * m.y;
+                p[1].y += x.y * m.x - x.x * m.y;
+            }
+            acc = fmk((p[0].x + p[1].x) + (p[2].x + p[3].x), (p[0].y + p[1].y) + (p[2].y + p[3].y));
         }
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 2);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 2);
+        if (valid && t4 == 0) {
+            const f2 da = Ap[a * LB - (a * (a - 1)) / 2];
+            f2 db = f2ld(Tf + (long long)(c0 + b) * ldf + c0 + b);
+            db.x -= sh;
+            const float dr = da.x + db.x, di = da.y - db.y;   // A_aa + conj(B_bb)
+            const float inv = 1.0f / (dr * dr + di * di);
+            const f2 v = fmk(Xs[a][b].x - acc.x, Xs[a][b].y - acc.y);
+            Xs[a][b] = fmk((v.x * dr + v.y * di) * inv, (v.y * dr - v.x * di) * inv);
+        }
+        __syncthreads();
     }
     // write back: complex128 block and the BF16 hi/lo planes of X (rows), lanes along q ...
     const long long ps = (long long)np * np;
@@ -159,7 +160,19 @@ k_sylv_leaf128(const cplx* __restrict__ T, cplx* __restrict__ X, int n, double s
     }
 }
 
-constexpr size_t LEAF_SMEM = sizeof(f2) * LB * PITCH + 2 * sizeof(f2) * SB * PITCH;
+// FP32 copies of T (row-major and transposed, zero padding), read by the leaf kernel through L1
+__global__ void k_t_to_f32(const cplx* __restrict__ T, int n, float2* __restrict__ Tf, float2* __restrict__ Ttf,
+                           int ld) {
+    const long long len = (long long)ld * ld;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / ld), j = (int)(e % ld);
+        const cplx v = (i < n && j < n) ? T[(long long)i * n + j] : cmake(0, 0);
+        Tf[e] = make_float2((float)v.x, (float)v.y);
+        Ttf[(long long)j * ld + i] = make_float2((float)v.x, (float)v.y);
+    }
+}
+
+constexpr size_t LEAF_SMEM = sizeof(f2) * LB * PITCH + sizeof(f2) * (LB * (LB + 1) / 2);
 
 inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
@@ -167,7 +180,7 @@ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
 size_t sylv_mixed_bytes(int n) {
     const size_t np = (size_t)round_up(n, LB);
-    return 3 * (4 * np * np * sizeof(__nv_bfloat16) + 256);
+    return 3 * (4 * np * np * sizeof(__nv_bfloat16) + 256) + 2 * (np * np * sizeof(float2) + 256);
 }
 
 int sylv_mixed_prepare(lb_handle_s* h, char* base, cudaStream_t s) {
@@ -185,6 +198,10 @@ int sylv_mixed_prepare(lb_handle_s* h, char* base, cudaStream_t s) {
     m->Tp = reinterpret_cast<__nv_bfloat16*>(carve(plane_bytes));
     m->Xp = reinterpret_cast<__nv_bfloat16*>(carve(plane_bytes));
     m->XTp = reinterpret_cast<__nv_bfloat16*>(carve(plane_bytes));
+    m->Tf = reinterpret_cast<float2*>(carve(np * np * sizeof(float2)));
+    m->Ttf = reinterpret_cast<float2*>(carve(np * np * sizeof(float2)));
+    k_t_to_f32<<<1184, 256, 0, s>>>(h->T, h->n, m->Tf, m->Ttf, (int)np);
+    lb_note_launch();
     if (cudaMemsetAsync(m->Xp, 0, plane_bytes, s) != cudaSuccess) return -1;
     if (cudaMemsetAsync(m->XTp, 0, plane_bytes, s) != cudaSuccess) return -1;
     if (tc_split_planes_bf16(h->T, h->n, h->n, h->n, 0, m->Tp, (int)np, (long long)np * np, s)) return -1;
@@ -231,7 +248,8 @@ int trisylv_mixed(lb_handle_s* h, cudaStream_t s, cplx* X, double shift) {
             p.wave = w;
             if (tc_gemm_launch(m->maps, p, cnt, 1, s)) return -1;
         }
-        k_sylv_leaf128<<<cnt, LEAF_THREADS, LEAF_SMEM, s>>>(h->T, X, h->n, shift, w, nb, m->Xp, m->XTp, m->np);
+        k_sylv_leaf128<<<cnt, LEAF_THREADS, LEAF_SMEM, s>>>(m->Tf, m->Ttf, m->np, X, h->n, (float)shift, w, nb, m->Xp,
+                                                             m->XTp, m->np);
         lb_note_launch();
         if (cudaGetLastError() != cudaSuccess) return -1;
     }
