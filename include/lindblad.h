@@ -160,6 +160,20 @@ lb_status steady_state(lindblad_handle h, void* rho_dev, const lb_opts* opts, lb
 lb_status low_spectrum(lindblad_handle h, int k, double mu, double eta, void* evals_host,
                        void* evecs_dev, const lb_opts* opts, lb_info* info, void* stream);
 
+/* Adjoint of the steady-state solve, for implicit differentiation (Remark "Differentiating the
+ * steady state").  Given the steady state rho (from steady_state) and a Hermitian observable O,
+ * solves L~_eta^* w = O (L~_eta^*(w) = G^dag w + w G + sum_j L_j^dag w L_j + eta Tr(w) I) by GMRES
+ * right-preconditioned with the adjoint no-jump resolvent (Schur coordinates, reversed-index
+ * triangular solve), refined against the FP64 adjoint residual until ||.||_max < opts->tol.
+ * Outputs (device, complex128, row-major): w (n x n); gH (n x n, nullable) and gL (d x n x n,
+ * nullable), the sensitivities of J = Tr(O rho) with dJ = Re<gH, dH> + sum_j Re<gL_j, dL_j>,
+ * <A, B> = Tr(A^dag B):  gH = i (rho w - w rho),  gL_j = -Ws L_j rho + 1/2 L_j (Ws rho + rho Ws),
+ * Ws = w + w^dag.  FP64 throughout.  Errors: LB_INVALID_ARG, LB_S_SINGULAR (case 1),
+ * LB_NOT_CONVERGED (best w and sensitivities returned). */
+lb_status steady_state_adjoint(lindblad_handle h, const void* rho_dev, const void* O_dev, void* w_dev,
+                               void* gH_dev, void* gL_dev, const lb_opts* opts, lb_info* info,
+                               void* stream);
+
 /* Kernel timing (diagnostics, no effect on results).  While enabled, the library records CUDA
  * events on the launching stream around every tensor-core GEMM launch (kernel id 0) and every
  * FP64 GEMM launch of the residual (kernel id 1).  lb_kernel_stats synchronises the stream and

@@ -34,6 +34,9 @@ struct lb_handle_s {
     cplx* X[NSCRATCH] = {};            // n x n scratch
     cplx* best = nullptr;              // n x n
     cplx* W = nullptr;                 // R_mu^S(I) for the Sherman-Morrison preconditioner
+    cplx* Wa = nullptr;                // its adjoint counterpart R_mu^{S*}(I)
+    cplx* Ua = nullptr;                // J T^dag J (J = index reversal): upper triangular, adjoint solves
+    bool ua_ready = false;
     cplx* V = nullptr;                 // inner Krylov basis (vcap vectors)
     cplx* Z = nullptr;                 // outer Krylov basis (vcap vectors)
     int vcap = 0;
@@ -88,6 +91,14 @@ lb_status steady_state_arnoldi(lb_handle_s* h, cudaStream_t s, const lb_opts& o,
 // solvers.cu
 int pure_state_case1(lb_handle_s* h, cudaStream_t s, cplx* rho_out);
 lb_status refine_steady_state(lb_handle_s* h, cudaStream_t s, const lb_opts& o, cplx* rho, lb_info* inf);
+
+lb_status adj_precond_prepare(lb_handle_s* h, cudaStream_t s, double eta);
+int adj_gmres_solve(lb_handle_s* h, cudaStream_t s, const cplx* b, cplx* x, double eta, int m, int max_cycles,
+                    double atol, int* steps, double* final_res);
+
+// adjoint.cu
+int adj_lyap_schur(lb_handle_s* h, cudaStream_t s, const cplx* Y, cplx* X, double shift);
+int adj_jump_f64(lb_handle_s* h, cudaStream_t s, const cplx* Z, cplx* Y, cplx alpha, cplx beta);
 
 // mixed.cu
 size_t mixed_bytes(int n, int d);

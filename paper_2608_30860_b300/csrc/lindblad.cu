@@ -73,6 +73,8 @@ void layout(lb_handle_s* h, char* base, int n, int d, const lb_opts* o, size_t s
     for (int i = 0; i < NSCRATCH; ++i) h->X[i] = c.take<cplx>(nn);
     h->best = c.take<cplx>(nn);
     h->W = c.take<cplx>(nn);
+    h->Wa = c.take<cplx>(nn);
+    h->Ua = c.take<cplx>(nn);
     h->vcap = krylov_cap(o) + 1;
     h->V = c.take<cplx>((size_t)h->vcap * nn);
     h->Z = c.take<cplx>((size_t)h->vcap * nn);

@@ -162,12 +162,14 @@ double read_double(cudaStream_t s, const double* d) {
 // ============================================================================ Alg. 2
 // W = R_mu^S(I) in Schur coordinates and its trace (scal[8]); returns LB_ETA_EXCLUDED if
 // |1 - eta Tr W| is negligible (Eq. ShermanMorr).
-static lb_status precond_prepare(lb_handle_s* h, cudaStream_t s, double mu, double eta, int precision) {
+static lb_status precond_prepare(lb_handle_s* h, cudaStream_t s, double mu, double eta, int precision, int adj) {
     const int n = h->n;
-    // (mu - S~) W = I  <=>  T_mu W + W T_mu^dag = -I
-    if (mat_eye(h->W, n, cmake(-1, 0), s)) return LB_CUDA_ERROR;
-    if (lyap_schur(h, s, h->W, h->W, 0.5 * mu, precision)) return LB_CUDA_ERROR;
-    if (mat_trace(h->W, n, h->scal + 8, s)) return LB_CUDA_ERROR;
+    cplx* W = adj ? h->Wa : h->W;
+    // (mu - S~) W = I  <=>  T_mu W + W T_mu^dag = -I   (adjoint: T_mu^dag W + W T_mu = -I)
+    if (mat_eye(W, n, cmake(-1, 0), s)) return LB_CUDA_ERROR;
+    if (adj ? adj_lyap_schur(h, s, W, W, 0.5 * mu) : lyap_schur(h, s, W, W, 0.5 * mu, precision))
+        return LB_CUDA_ERROR;
+    if (mat_trace(W, n, h->scal + 8, s)) return LB_CUDA_ERROR;
     cplx trw;
     LB_CHECK_CUDA(cudaMemcpyAsync(&trw, h->scal + 8, sizeof(cplx), cudaMemcpyDeviceToHost, s));
     LB_CHECK_CUDA(cudaStreamSynchronize(s));
@@ -178,12 +180,13 @@ static lb_status precond_prepare(lb_handle_s* h, cudaStream_t s, double mu, doub
 
 // out = Precond(X, mu, eta) = Z + eta Tr Z / (1 - eta Tr W) W, Z = R_mu^S(X)  (Alg. 2)
 static int precond_apply(lb_handle_s* h, cudaStream_t s, const cplx* X, cplx* out, double mu, double eta,
-                         int precision) {
+                         int precision, int adj) {
     const long long nn = (long long)h->n * h->n;
     if (vec_scale_copy(out, X, nn, cmake(-1, 0), s)) return -1;                // -X
-    if (lyap_schur(h, s, out, out, 0.5 * mu, precision)) return -1;            // Z
+    if (adj ? adj_lyap_schur(h, s, out, out, 0.5 * mu) : lyap_schur(h, s, out, out, 0.5 * mu, precision))
+        return -1;                                                               // Z
     if (mat_trace(out, h->n, h->scal + 9, s)) return -1;
-    k_sm_combine<<<grid1(nn), 256, 0, s>>>(out, h->W, nn, h->scal + 9, h->scal + 8, eta); lb_note_launch();
+    k_sm_combine<<<grid1(nn), 256, 0, s>>>(out, adj ? h->Wa : h->W, nn, h->scal + 9, h->scal + 8, eta); lb_note_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -223,7 +226,7 @@ __global__ void k_gmres_resid_coeffs(const cplx* Hb, int ldh, int k, double beta
 // residual norm <= atol, on stagnation (< 10% gain per cycle) or after max_cycles.
 // Uses V / hm (inner basis), X[5], X[6], X[7].
 static int gmres_solve(lb_handle_s* h, cudaStream_t s, const cplx* b, cplx* x, double mu, double eta, int m,
-                       int max_cycles, double atol, int precision, int* steps, double* final_res) {
+                       int max_cycles, double atol, int precision, int* steps, double* final_res, int adj = 0) {
     const long long nn = (long long)h->n * h->n;
     cplx* r = h->X[5];
     cplx* pv = h->X[6];
@@ -231,8 +234,10 @@ static int gmres_solve(lb_handle_s* h, cudaStream_t s, const cplx* b, cplx* x, d
     cplx* g = h->ev;   // (k+1) residual coefficients
     double* dres = h->dscal + 6;
     OpFn op = [&](const cplx* v, cplx* w) {
-        if (precond_apply(h, s, v, pv, mu, eta, precision)) return -1;
-        if (precision == LB_PREC_MIXED && h->mixed_ready) {
+        if (precond_apply(h, s, v, pv, mu, eta, precision, adj)) return -1;
+        if (adj) {
+            if (adj_jump_f64(h, s, pv, w, cmake(-1, 0), cmake(0, 0))) return -1;
+        } else if (precision == LB_PREC_MIXED && h->mixed_ready) {
             if (jump_mixed(h, s, pv, w, -1.0)) return -1;
         } else if (jump_f64(h, s, h->Lt, pv, w, cmake(-1, 0), cmake(0, 0))) {
             return -1;
@@ -251,7 +256,7 @@ static int gmres_solve(lb_handle_s* h, cudaStream_t s, const cplx* b, cplx* x, d
         *steps += k;
         k_hess_lstsq<<<1, 32, 0, s>>>(h->hm, h->ldh, k, beta, h->evec, y, dres); lb_note_launch();
         if (vec_gemv(r, h->V, nn, k, y, nn, 1.0, 0, s)) return -1;           // u = V y
-        if (precond_apply(h, s, r, pv, mu, eta, precision)) return -1;     // P u
+        if (precond_apply(h, s, r, pv, mu, eta, precision, adj)) return -1;   // P u
         if (vec_axpby(x, pv, nn, cmake(1, 0), cmake(1, 0), s)) return -1;  // x += P u
         k_gmres_resid_coeffs<<<1, 64, 0, s>>>(h->hm, h->ldh, k, beta, y, g); lb_note_launch();
         if (vec_gemv(r, h->V, nn, k + 1, g, nn, 1.0, 0, s)) return -1;      // r = V_{k+1} g
@@ -262,6 +267,15 @@ static int gmres_solve(lb_handle_s* h, cudaStream_t s, const cplx* b, cplx* x, d
     }
     *final_res = res;
     return 0;
+}
+
+// entry points for the adjoint solve (adjoint.cu)
+lb_status adj_precond_prepare(lb_handle_s* h, cudaStream_t s, double eta) {
+    return precond_prepare(h, s, 0.0, eta, LB_PREC_FP64, 1);
+}
+int adj_gmres_solve(lb_handle_s* h, cudaStream_t s, const cplx* b, cplx* x, double eta, int m, int max_cycles,
+                    double atol, int* steps, double* final_res) {
+    return gmres_solve(h, s, b, x, 0.0, eta, m, max_cycles, atol, LB_PREC_FP64, steps, final_res, 1);
 }
 
 // ============================================================================ case 1
@@ -284,7 +298,7 @@ int pure_state_case1(lb_handle_s* h, cudaStream_t s, cplx* rho_out) {
 lb_status refine_steady_state(lb_handle_s* h, cudaStream_t s, const lb_opts& o, cplx* rho, lb_info* inf) {
     const int n = h->n;
     const long long nn = (long long)n * n;
-    lb_status st = precond_prepare(h, s, 0.0, o.eta, o.precision);
+    lb_status st = precond_prepare(h, s, 0.0, o.eta, o.precision, 0);
     if (st != LB_OK) return st;
     cplx* R = h->X[1];
     cplx* rt = h->X[2];
@@ -332,7 +346,7 @@ extern "C" lb_status low_spectrum(lindblad_handle h, int k, double mu, double et
     inf.schur_backward_err = h->schur_err;
     inf.min_abs_re_T = h->min_re_T;
     inf.setup_ms = h->setup_ms;
-    lb_status st = precond_prepare(h, s, mu, eta, o.precision);
+    lb_status st = precond_prepare(h, s, mu, eta, o.precision, 0);
     if (st != LB_OK) return st;
     // the outer relation matrix is read as a general matrix by the small Schur kernel: clear it
     LB_CHECK_CUDA(cudaMemsetAsync(h->hm2, 0, (size_t)(KMAX + 1) * (KMAX + 1) * sizeof(cplx), s));

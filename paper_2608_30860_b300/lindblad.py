@@ -81,6 +81,8 @@ def load_library(path: str = LIB_PATH):
     lib.steady_state.restype = i
     lib.low_spectrum.argtypes = [vp, i, d, d, vp, vp, P(LbOpts), P(LbInfo), vp]
     lib.low_spectrum.restype = i
+    lib.steady_state_adjoint.argtypes = [vp, vp, vp, vp, vp, vp, P(LbOpts), P(LbInfo), vp]
+    lib.steady_state_adjoint.restype = i
     lib.lindblad_destroy.argtypes = [vp]
     lib.lindblad_destroy.restype = None
     lib.lb_set_profiling.argtypes = [vp, i]
@@ -233,6 +235,25 @@ def lb_kernel_stats(h: Handle, kernel: int = 0):
 def lb_launch_count() -> int:
     """Kernels launched by the library in this process so far."""
     return int(load_library().lb_launch_count())
+
+
+def steady_state_adjoint(h: Handle, rho: torch.Tensor, O: torch.Tensor, opts: LbOpts | None = None,
+                         want_sensitivities: bool = True):
+    """Adjoint state w of L~_eta^* w = O and the sensitivities (gH, gL) of J = Tr(O rho):
+    dJ = Re<gH, dH> + sum_j Re<gL_j, dL_j>.  Returns (w, gH, gL, info, status)."""
+    o = opts or default_opts()
+    dev = h.workspace.device
+    w = torch.empty((h.n, h.n), dtype=torch.complex128, device=dev)
+    gH = torch.empty_like(w) if want_sensitivities else None
+    gL = torch.empty((h.d, h.n, h.n), dtype=torch.complex128, device=dev) if want_sensitivities else None
+    info = LbInfo()
+    st = load_library().steady_state_adjoint(h.ptr, _dev(rho, (h.n, h.n)), _dev(O, (h.n, h.n)), w.data_ptr(),
+                                             None if gH is None else gH.data_ptr(),
+                                             None if gL is None else gL.data_ptr(), ctypes.byref(o),
+                                             ctypes.byref(info), _stream())
+    if st < 0 or st == 2:
+        raise LindbladError(st, "steady_state_adjoint")
+    return w, gH, gL, info.as_dict(), st
 
 
 def lindblad_destroy(h: Handle):

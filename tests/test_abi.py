@@ -29,6 +29,7 @@ def lib():
 def test_header_declares_the_boundary():
     names = _declared_functions()
     for required in ("lindblad_setup", "phi_apply", "jump_apply", "steady_state", "low_spectrum", "lindblad_destroy",
+                     "steady_state_adjoint",
                      "lindblad_workspace_bytes", "resolvent_apply", "lindbladian_apply"):
         assert required in names
 
