@@ -73,7 +73,16 @@ typedef struct {
     double inner_tol;     /* shift-invert inner GMRES relative tolerance (default 1e-10); a solve also
                              stops when one restart cycle reduces its residual by less than 10% */
     int    keep_ritz;     /* p of Alg. 5: Ritz pairs kept at a thick restart (default 0 = auto) */
+    int    route;         /* Lyapunov route of the FP64 path (lb_route, default LB_ROUTE_SCHUR); read at
+                             set-up */
+    double eig_cond_max;  /* cond(U) gate of the eigenbasis route (default 1e3): the route is used only if
+                             ||R||_F ||R^{-1}||_F / n <= eig_cond_max, R = Q^dag U */
 } lb_opts;
+
+/* Lyapunov route: Bartels-Stewart on the Schur form (App. A.1.1), or the eigenbasis divide of Alg. 1
+ * (App. A.1.2) in Schur coordinates, X = R[(R^{-1} Y R^{-dag}) o D]R^dag with D_ij = 1/(s_i + s_j^* - lam)
+ * and G = Q T Q^dag = (Q R) diag(s) (Q R)^{-1}; AUTO takes the eigenbasis route when the gate passes. */
+typedef enum { LB_ROUTE_SCHUR = 0, LB_ROUTE_EIG = 1, LB_ROUTE_AUTO = 2 } lb_route;
 
 typedef struct {
     int    status;
@@ -88,6 +97,8 @@ typedef struct {
     double min_abs_re_T;      /* min_i |Re T_ii| (case-1 test of Theorem 1) */
     double setup_ms;          /* lindblad_setup wall time (host clock around the stream) */
     double solve_ms;          /* wall time of the call that filled this struct */
+    double cond_eig;          /* ||R||_F ||R^{-1}||_F / n of the eigenbasis (0 if not computed) */
+    int    route;             /* Lyapunov route in use (lb_route) */
 } lb_info;
 
 typedef struct lb_handle_s* lindblad_handle;
@@ -106,9 +117,12 @@ size_t lindblad_workspace_bytes(int n, int d, const lb_opts* opts);
  * Copies H and L into the workspace, forms G = -iH - 1/2 sum_j L_j^dag L_j with one
  * stacked GEMM, computes the Schur form G = Q T Q^dag (eigenvectors -> QR -> upper
  * triangle of Q^dag G Q), the Schur-coordinate jump operators L~_j = Q^dag L_j Q and the
- * case-1 test of Theorem 1.  On success *out receives a handle.
- * Errors: LB_INVALID_ARG (n < 2, d < 1, null pointers), LB_WORKSPACE_TOO_SMALL,
- * LB_SOLVER_ERROR, LB_CUDA_ERROR.  info (nullable) receives set-up diagnostics. */
+ * case-1 test of Theorem 1.  With opts->route != LB_ROUTE_SCHUR it also keeps R = Q^dag U and
+ * R^{-1} for the eigenbasis route and applies the cond(U) gate.  On success *out receives a handle.
+ * Returns LB_OK, or LB_ILL_CONDITIONED (handle valid, Schur route in use) when LB_ROUTE_EIG was
+ * requested and the gate refused it.  Errors: LB_INVALID_ARG (n < 2, d < 1, null pointers),
+ * LB_WORKSPACE_TOO_SMALL, LB_SOLVER_ERROR, LB_CUDA_ERROR.  info (nullable) receives set-up
+ * diagnostics. */
 lb_status lindblad_setup(const void* H_dev, const void* L_dev, int n, int d,
                          void* workspace_dev, size_t workspace_bytes, void* stream,
                          const lb_opts* opts, lindblad_handle* out, lb_info* info);

@@ -36,6 +36,12 @@ struct lb_handle_s {
     cplx* W = nullptr;                 // R_mu^S(I) for the Sherman-Morrison preconditioner
     cplx* Wa = nullptr;                // its adjoint counterpart R_mu^{S*}(I)
     cplx* Ua = nullptr;                // J T^dag J (J = index reversal): upper triangular, adjoint solves
+    cplx* Re = nullptr;                // R = Q^dag U (eigenbasis route), upper triangular
+    cplx* Rinv = nullptr;              // R^{-1}
+    cplx* E1 = nullptr;                // eigenbasis-route scratch (n x n each)
+    cplx* E2 = nullptr;
+    bool eig_active = false;           // FP64 Lyapunov solves use the eigenbasis route
+    double cond_eig = 0.0;
     bool ua_ready = false;
     cplx* V = nullptr;                 // inner Krylov basis (vcap vectors)
     cplx* Z = nullptr;                 // outer Krylov basis (vcap vectors)
@@ -80,6 +86,7 @@ int jump_f64(lb_handle_s* h, cudaStream_t s, const cplx* Ls, const cplx* Z, cplx
 int lindbladian_f64(lb_handle_s* h, cudaStream_t s, const cplx* X, cplx* R);
 int change_basis(lb_handle_s* h, cudaStream_t s, const cplx* X, cplx* Out, cplx* tmp, int to_schur);
 int lyap_schur(lb_handle_s* h, cudaStream_t s, const cplx* Y, cplx* X, double shift, int precision);
+int lyap_eig(lb_handle_s* h, cudaStream_t s, const cplx* Y, cplx* X, double shift);
 int phi_schur(lb_handle_s* h, cudaStream_t s, const cplx* X, cplx* Y, int form, int precision);
 int arnoldi_cycle(lb_handle_s* h, cudaStream_t s, cplx* basis, cplx* hess, int j0, int m, const OpFn& op,
                   int* k_out);

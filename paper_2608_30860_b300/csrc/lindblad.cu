@@ -52,6 +52,11 @@ size_t cusolver_ws_bytes(int n, size_t* host_bytes) {
     cusolverDnXgeqrf_bufferSize(hs, prm, n, n, CUDA_C_64F, nullptr, n, CUDA_C_64F, nullptr, CUDA_C_64F, &dev_qr,
                                 &host_qr);
     cusolverDnZungqr_bufferSize(hs, n, n, n, nullptr, n, nullptr, &lwork);
+    size_t dev_tri = 0, host_tri = 0;
+    cusolverDnXtrtri_bufferSize(hs, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, n, CUDA_C_64F, nullptr, n, &dev_tri,
+                                &host_tri);
+    dev_qr = std::max(dev_qr, dev_tri);
+    host_qr = std::max(host_qr, host_tri);
     cusolverDnDestroyParams(prm);
     cusolverDnDestroy(hs);
     if (host_bytes) *host_bytes = std::max(host_geev, host_qr);
@@ -75,6 +80,10 @@ void layout(lb_handle_s* h, char* base, int n, int d, const lb_opts* o, size_t s
     h->W = c.take<cplx>(nn);
     h->Wa = c.take<cplx>(nn);
     h->Ua = c.take<cplx>(nn);
+    h->Re = c.take<cplx>(nn);
+    h->Rinv = c.take<cplx>(nn);
+    h->E1 = c.take<cplx>(nn);
+    h->E2 = c.take<cplx>(nn);
     h->vcap = krylov_cap(o) + 1;
     h->V = c.take<cplx>((size_t)h->vcap * nn);
     h->Z = c.take<cplx>((size_t)h->vcap * nn);
@@ -183,7 +192,21 @@ int lyap_schur(lb_handle_s* h, cudaStream_t s, const cplx* Y, cplx* X, double sh
     const long long nn = (long long)h->n * h->n;
     if (X != Y) LB_CHECK_CUDA(cudaMemcpyAsync(X, Y, nn * sizeof(cplx), cudaMemcpyDeviceToDevice, s));
     if (precision == LB_PREC_MIXED && h->mixed_sylv_ready) return trisylv_mixed(h, s, X, shift);
+    if (h->eig_active) return lyap_eig(h, s, X, X, shift);
     return trisylv_f64(h->T, X, h->n, cmake(shift, 0.0), s);
+}
+
+// eigenbasis route (Alg. 1) in Schur coordinates: X = R[(R^{-1} Y R^{-dag}) o D]R^dag,
+// D_ij = 1 / (s_i + conj(s_j) - 2 shift), s = diag(T); Y and X may alias
+int lyap_eig(lb_handle_s* h, cudaStream_t s, const cplx* Y, cplx* X, double shift) {
+    const int n = h->n;
+    cplx* t = h->E1;
+    cplx* yh = h->E2;
+    if (gemm(h, s, t, h->Rinv, OP_N, Y, OP_N, n, n, n, cmake(1, 0), cmake(0, 0))) return -1;
+    if (gemm(h, s, yh, t, OP_N, h->Rinv, OP_C, n, n, n, cmake(1, 0), cmake(0, 0))) return -1;
+    if (mat_eig_divide(yh, h->T, n, shift, s)) return -1;
+    if (gemm(h, s, t, h->Re, OP_N, yh, OP_N, n, n, n, cmake(1, 0), cmake(0, 0))) return -1;
+    return gemm(h, s, X, t, OP_N, h->Re, OP_C, n, n, n, cmake(1, 0), cmake(0, 0));
 }
 
 // Schur-coordinate Phi (form 0) or M (form 1): Y = -K~ S~^{-1} X  or  Y = -S~^{-1} K~ X
@@ -310,6 +333,8 @@ void lb_default_opts(lb_opts* o) {
     o->sylv_block = 0;
     o->inner_tol = 1e-10;
     o->keep_ritz = 0;
+    o->route = LB_ROUTE_SCHUR;
+    o->eig_cond_max = 1e3;
 }
 
 const char* lb_status_string(int st) {
@@ -415,6 +440,25 @@ lb_status lindblad_setup(const void* H_dev, const void* L_dev, int n, int d, voi
             if (cs == CUSOLVER_STATUS_SUCCESS)
                 cs = cusolverDnXgeqrf(hs, prm, n, n, CUDA_C_64F, VR, n, CUDA_C_64F, tau, CUDA_C_64F, h->solver_ws,
                                       h->solver_ws_bytes, hbuf.data(), hbuf.size(), h->dinfo);
+            // eigenbasis route: R = Q^dag U is the triangular QR factor held in VR's upper triangle
+            if (cs == CUSOLVER_STATUS_SUCCESS && o.route != LB_ROUTE_SCHUR) {
+                cplx* Rcm = h->X[4];
+                if (mat_transpose(h->X[5], VR, n, s) || mat_take_upper(h->Re, h->X[5], n, h->dpart, h->dscal + 6, s) ||
+                    cudaMemcpyAsync(Rcm, VR, (size_t)nn * sizeof(cplx), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+                    cs = CUSOLVER_STATUS_EXECUTION_FAILED;
+                size_t dt = 0, ht = 0;
+                if (cs == CUSOLVER_STATUS_SUCCESS)
+                    cs = cusolverDnXtrtri_bufferSize(hs, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, n, CUDA_C_64F,
+                                                     Rcm, n, &dt, &ht);
+                if (ht > hbuf.size()) hbuf.resize(ht);
+                if (cs == CUSOLVER_STATUS_SUCCESS && dt > h->solver_ws_bytes) cs = CUSOLVER_STATUS_ALLOC_FAILED;
+                if (cs == CUSOLVER_STATUS_SUCCESS)
+                    cs = cusolverDnXtrtri(hs, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, n, CUDA_C_64F, Rcm, n,
+                                          h->solver_ws, h->solver_ws_bytes, hbuf.data(), hbuf.size(), h->dinfo);
+                if (cs == CUSOLVER_STATUS_SUCCESS &&
+                    (mat_transpose(h->X[5], Rcm, n, s) || mat_take_upper(h->Rinv, h->X[5], n, h->dpart, h->dscal + 6, s)))
+                    cs = CUSOLVER_STATUS_EXECUTION_FAILED;
+            }
             int lwork = 0;
             if (cs == CUSOLVER_STATUS_SUCCESS)
                 cs = cusolverDnZungqr_bufferSize(hs, n, n, n, (cuDoubleComplex*)VR, n, (cuDoubleComplex*)tau, &lwork);
@@ -464,6 +508,17 @@ lb_status lindblad_setup(const void* H_dev, const void* L_dev, int n, int d, voi
     h->schur_err = diag[1] / std::max(diag[3], 1e-300);
     h->min_re_T = diag[4];
     h->case1 = h->min_re_T <= 1e3 * 2.220446049250313e-16 * h->gnorm;
+    lb_status ret = LB_OK;
+    if (o.route != LB_ROUTE_SCHUR) {
+        double nr[4];
+        if (vec_norms(h->Re, nn, h->dpart, h->dscal + 8, s) || vec_norms(h->Rinv, nn, h->dpart, h->dscal + 10, s) ||
+            cudaMemcpyAsync(nr, h->dscal + 8, 4 * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return fail(LB_CUDA_ERROR);
+        h->cond_eig = nr[1] * nr[3] / n;
+        h->eig_active = !h->case1 && std::isfinite(h->cond_eig) && h->cond_eig <= o.eig_cond_max;
+        if (o.route == LB_ROUTE_EIG && !h->eig_active) ret = LB_ILL_CONDITIONED;
+    }
     if (cudaMemsetAsync(h->dinfo, 0, 16 * sizeof(int), s) != cudaSuccess) return fail(LB_CUDA_ERROR);
     if (mixed_prepare(h, s)) return fail(LB_CUDA_ERROR);
     if (cudaStreamSynchronize(s) != cudaSuccess) return fail(LB_CUDA_ERROR);
@@ -473,10 +528,12 @@ lb_status lindblad_setup(const void* H_dev, const void* L_dev, int n, int d, voi
         info->schur_backward_err = h->schur_err;
         info->min_abs_re_T = h->min_re_T;
         info->setup_ms = h->setup_ms;
-        info->status = h->case1 ? LB_S_SINGULAR : LB_OK;
+        info->cond_eig = h->cond_eig;
+        info->route = h->eig_active ? LB_ROUTE_EIG : LB_ROUTE_SCHUR;
+        info->status = h->case1 ? LB_S_SINGULAR : ret;
     }
     *out = h;
-    return LB_OK;
+    return ret;
 }
 
 void lindblad_destroy(lindblad_handle h) {
@@ -584,6 +641,8 @@ lb_status steady_state(lindblad_handle h, void* rho_dev, const lb_opts* opts, lb
     inf.schur_backward_err = h->schur_err;
     inf.min_abs_re_T = h->min_re_T;
     inf.setup_ms = h->setup_ms;
+    inf.cond_eig = h->cond_eig;
+    inf.route = h->eig_active && o.precision == LB_PREC_FP64 ? LB_ROUTE_EIG : LB_ROUTE_SCHUR;
     lb_status st = LB_OK;
     if (h->case1) {
         // Theorem 1, case 1: pure steady state from the eigenvector of G on the imaginary axis

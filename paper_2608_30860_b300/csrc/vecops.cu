@@ -248,6 +248,16 @@ __global__ void k_min_abs_re_diag(const cplx* T, int n, double* out) {
     }
 }
 
+// X_ij /= (T_ii + conj(T_jj) - 2 shift)  (eigenbasis divide; T's diagonal holds the eigenvalues)
+__global__ void k_eig_divide(cplx* X, const cplx* T, int n, double shift) {
+    const long long len = (long long)n * n;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / n), j = (int)(e % n);
+        const cplx si = T[(long long)i * n + i], sj = T[(long long)j * n + j];
+        X[e] = cdiv(X[e], cmake(si.x + sj.x - 2.0 * shift, si.y - sj.y));
+    }
+}
+
 inline int grid_for(long long len) {
     long long g = (len + RT - 1) / RT;
     if (g > 148 * 8) g = 148 * 8;
@@ -332,6 +342,11 @@ int mat_transpose(cplx* Y, const cplx* X, int n, cudaStream_t s) {
 int mat_take_upper(cplx* T, const cplx* A, int n, double* part, double* out, cudaStream_t s) {
     k_take_upper<<<DOT_BLOCKS, RT, 0, s>>>(T, A, n, part); lb_note_launch();
     k_norms_final<<<1, 32, 0, s>>>(part, DOT_BLOCKS, out); lb_note_launch();
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int mat_eig_divide(cplx* X, const cplx* T, int n, double shift, cudaStream_t s) {
+    k_eig_divide<<<grid_for((long long)n * n), RT, 0, s>>>(X, T, n, shift); lb_note_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

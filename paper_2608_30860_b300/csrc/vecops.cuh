@@ -25,6 +25,8 @@ int mat_transpose(cplx* Y, const cplx* X, int n, cudaStream_t s);
 // T = upper(A); out[1] = ||strictly-lower(A)||_F
 int mat_take_upper(cplx* T, const cplx* A, int n, double* part, double* out, cudaStream_t s);
 int mat_min_abs_re_diag(const cplx* T, int n, double* out, cudaStream_t s);
+// X_ij /= (T_ii + conj(T_jj) - 2 shift)
+int mat_eig_divide(cplx* X, const cplx* T, int n, double shift, cudaStream_t s);
 
 // small dense eigensolver for an m x m upper-Hessenberg matrix (m <= 64), hess.cu
 int hess_eig(const cplx* H, int ldh, int m, cplx* evals, cplx* evecs, int* info, cudaStream_t s);

@@ -20,6 +20,9 @@ LB_PREC_FP64 = 0
 LB_PREC_MIXED = 1
 LB_APPLY_FORM_M = 1
 LB_APPLY_SCHUR = 2
+LB_ROUTE_SCHUR = 0
+LB_ROUTE_EIG = 1
+LB_ROUTE_AUTO = 2
 
 STATUS = {0: "LB_OK", 1: "LB_NOT_CONVERGED", 2: "LB_S_SINGULAR", 3: "LB_ILL_CONDITIONED",
           -1: "LB_INVALID_ARG", -2: "LB_CUDA_ERROR", -3: "LB_ETA_EXCLUDED",
@@ -36,7 +39,7 @@ class LbOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("krylov_m", ctypes.c_int), ("max_restarts", ctypes.c_int),
                 ("precision", ctypes.c_int), ("eta", ctypes.c_double), ("max_refine", ctypes.c_int),
                 ("gmres_m", ctypes.c_int), ("sylv_block", ctypes.c_int), ("inner_tol", ctypes.c_double),
-                ("keep_ritz", ctypes.c_int)]
+                ("keep_ritz", ctypes.c_int), ("route", ctypes.c_int), ("eig_cond_max", ctypes.c_double)]
 
 
 class LbInfo(ctypes.Structure):
@@ -44,7 +47,8 @@ class LbInfo(ctypes.Structure):
                 ("gmres_steps", ctypes.c_int), ("refine_steps", ctypes.c_int),
                 ("residual_max", ctypes.c_double), ("residual_fro", ctypes.c_double),
                 ("ritz_value", ctypes.c_double), ("schur_backward_err", ctypes.c_double),
-                ("min_abs_re_T", ctypes.c_double), ("setup_ms", ctypes.c_double), ("solve_ms", ctypes.c_double)]
+                ("min_abs_re_T", ctypes.c_double), ("setup_ms", ctypes.c_double), ("solve_ms", ctypes.c_double),
+                ("cond_eig", ctypes.c_double), ("route", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -43,8 +43,9 @@ def test_opts_struct_layout_and_defaults(lib):
     from paper_2608_30860_b300 import lindblad as B
     o = B.default_opts()
     assert o.tol == 1e-10 and o.krylov_m == 20 and o.gmres_m == 40 and o.eta == 1.0 and o.precision == B.LB_PREC_FP64
-    assert ctypes.sizeof(B.LbOpts) == 64   # C layout: 3 doubles, 7 ints, natural padding
-    assert ctypes.sizeof(B.LbInfo) == 80
+    assert o.route == B.LB_ROUTE_SCHUR and o.eig_cond_max == 1e3
+    assert ctypes.sizeof(B.LbOpts) == 72   # C layout: 4 doubles, 8 ints, natural padding
+    assert ctypes.sizeof(B.LbInfo) == 96
 
 
 def test_invalid_sizes_rejected_on_host(lib):

@@ -203,3 +203,40 @@ def test_eta_excluded_value_rejected(B):
         B.low_spectrum(h, 2, mu=0.0, eta=eta_bad, opts=opts)
     assert e.value.status == -3
     B.lindblad_destroy(h)
+
+
+@pytest.mark.parametrize("lam", [0.0, 0.6])
+def test_eigenbasis_route_matches_schur_route_and_oracle(B, lam):
+    """Alg. 1 (eigenbasis divide, in Schur coordinates via R = Q^dag U) against Bartels-Stewart and
+    the oracle's eigen route; well-conditioned random system (cond ~ 8 << gate 1e3)."""
+    H, Ls = gi.random_lindbladian(96, d=3, seed=21)
+    n = 96
+    he, oe = _setup(B, H, Ls, route=B.LB_ROUTE_EIG)
+    assert he.setup_info["route"] == B.LB_ROUTE_EIG and 1.0 <= he.setup_info["cond_eig"] < 1e3
+    hs, _ = _setup(B, H, Ls)
+    Y = gi.random_operator(n, seed=2)
+    ge = B.resolvent_apply(he, _cuda(Y), lam).cpu().numpy()
+    gs = B.resolvent_apply(hs, _cuda(Y), lam).cpu().numpy()
+    ref = K.System(H, Ls, route="eig").resolvent_S(Y, lam)
+    assert _rel(ge, ref) < 1e-11 and _rel(ge, gs) < 1e-11
+    rho, info, st = B.steady_state(he, B.default_opts(tol=1e-13, route=B.LB_ROUTE_EIG))
+    assert st == 0 and info["route"] == B.LB_ROUTE_EIG and info["residual_max"] < 1e-13
+    rho_s, _, st_s = B.steady_state(hs, B.default_opts(tol=1e-13))
+    rho, rho_s = rho.cpu().numpy(), rho_s.cpu().numpy()
+    assert np.linalg.norm(rho - rho_s) / np.linalg.norm(rho_s) < 1e-10
+    B.lindblad_destroy(he)
+    B.lindblad_destroy(hs)
+
+
+def test_eigenbasis_route_gate_refuses(B):
+    """With the gate below the system's cond(U) the set-up reports LB_ILL_CONDITIONED (3) and keeps
+    the Schur route, whose results stay exact."""
+    H, Ls = gi.random_lindbladian(40, d=2, seed=5)
+    opts = B.default_opts(route=B.LB_ROUTE_EIG, eig_cond_max=1.0)
+    h = B.lindblad_setup(_cuda(H), _cuda(np.stack(Ls)), opts)
+    assert h.setup_info["status"] == 3 and h.setup_info["route"] == B.LB_ROUTE_SCHUR
+    assert h.setup_info["cond_eig"] > 1.0
+    X = gi.random_operator(40, seed=1)
+    ref = D.unvec(D.Phi_super(H, Ls) @ D.vec(X), 40)
+    assert _rel(B.phi_apply(h, _cuda(X)).cpu().numpy(), ref) < 1e-11
+    B.lindblad_destroy(h)
