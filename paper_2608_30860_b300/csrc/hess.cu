@@ -15,49 +15,9 @@
 #include "common.cuh"
 #include "vecops.cuh"
 
+#include "small_schur.cuh"
+
 namespace {
-
-__device__ __forceinline__ double cabsd(cplx a) { return hypot(a.x, a.y); }
-
-__device__ cplx csqrt_d(cplx z) {
-    double r = cabsd(z);
-    if (r == 0.0) return cmake(0.0, 0.0);
-    double t = sqrt(0.5 * (r + fabs(z.x)));
-    if (z.x >= 0.0) return cmake(t, z.y / (2.0 * t));
-    return cmake(fabs(z.y) / (2.0 * t), z.y >= 0.0 ? t : -t);
-}
-
-// c real, s complex with [c s; -conj(s) c] [x; y] = [r; 0]
-__device__ void givens(cplx x, cplx y, double& c, cplx& s) {
-    double ax = cabsd(x), ay = cabsd(y);
-    if (ay == 0.0) { c = 1.0; s = cmake(0.0, 0.0); return; }
-    if (ax == 0.0) { c = 0.0; s = cscale(cconj(y), 1.0 / ay); return; }
-    double r = hypot(ax, ay);
-    c = ax / r;
-    s = cscale(cmul(cscale(x, 1.0 / ax), cconj(y)), 1.0 / r);
-}
-
-// rows k, k+1 of A (columns j0..m-1) <- G [row k; row k+1]
-__device__ void rot_rows(cplx* A, int m, int k, int j0, double c, cplx s, int lane) {
-    for (int j = j0 + lane; j < m; j += 32) {
-        cplx a = A[k * m + j], b = A[(k + 1) * m + j];
-        A[k * m + j] = cadd(cscale(a, c), cmul(s, b));
-        A[(k + 1) * m + j] = csub(cscale(b, c), cmul(cconj(s), a));
-    }
-}
-// columns k, k+1 of A (rows 0..imax) <- [col k, col k+1] G^dag
-__device__ void rot_cols(cplx* A, int m, int k, int imax, double c, cplx s, int lane) {
-    for (int i = lane; i <= imax; i += 32) {
-        cplx a = A[i * m + k], b = A[i * m + k + 1];
-        A[i * m + k] = cadd(cscale(a, c), cmul(b, cconj(s)));
-        A[i * m + k + 1] = csub(cscale(b, c), cmul(a, s));
-    }
-}
-
-__device__ double order_key(cplx v, int order) {
-    if (order == 1) return cabsd(v);                                   // largest |nu| first
-    return -cabsd(csub(v, cmake(1.0, 0.0))) + 1e-300 * v.x;            // nearest 1 first
-}
 
 __global__ void k_small_schur(const cplx* __restrict__ Ain, int lda, int m, int hess_in, int order, int nsel,
                               cplx* __restrict__ evals, cplx* __restrict__ evecs, cplx* __restrict__ Tout,
@@ -69,196 +29,7 @@ __global__ void k_small_schur(const cplx* __restrict__ Ain, int lda, int m, int 
     __shared__ cplx hv[64];
     __shared__ cplx rot_s;
     __shared__ double rot_c;
-    const int lane = threadIdx.x;
-    const double eps = 2.220446049250313e-16;
-
-    for (int e = lane; e < m * m; e += 32) {
-        int i = e / m, j = e % m;
-        cplx a = Ain[(long long)j * lda + i];             // column-major input
-        if (hess_in && i > j + 1) a = cmake(0.0, 0.0);
-        A[e] = a;
-        Z[e] = cmake(i == j ? 1.0 : 0.0, 0.0);
-    }
-    __syncwarp();
-
-    // 1. Householder reduction to Hessenberg form
-    if (!hess_in) {
-        for (int k = 0; k + 2 < m; ++k) {
-            double nrm2 = 0.0;
-            for (int i = k + 1 + lane; i < m; i += 32) nrm2 += cabs2(A[i * m + k]);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) nrm2 += __shfl_xor_sync(0xffffffffu, nrm2, o);
-            double xn = sqrt(nrm2);
-            cplx x0 = A[(k + 1) * m + k];
-            double sub = xn * xn - cabs2(x0);
-            if (xn == 0.0 || sub <= 1e-300 * xn * xn) continue;      // already zero below subdiagonal
-            double ax0 = cabsd(x0);
-            cplx ph = ax0 > 0.0 ? cscale(x0, 1.0 / ax0) : cmake(1.0, 0.0);
-            cplx alpha = cscale(ph, -xn);
-            // v = x - alpha e1, normalised
-            for (int i = k + 1 + lane; i < m; i += 32) hv[i] = A[i * m + k];
-            __syncwarp();
-            if (lane == 0) hv[k + 1] = csub(hv[k + 1], alpha);
-            __syncwarp();
-            double vn = 0.0;
-            for (int i = k + 1 + lane; i < m; i += 32) vn += cabs2(hv[i]);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) vn += __shfl_xor_sync(0xffffffffu, vn, o);
-            double inv = 1.0 / sqrt(vn);
-            for (int i = k + 1 + lane; i < m; i += 32) hv[i] = cscale(hv[i], inv);
-            __syncwarp();
-            // A <- (I - 2 v v^H) A
-            for (int j = k + lane; j < m; j += 32) {
-                cplx sacc = cmake(0.0, 0.0);
-                for (int i = k + 1; i < m; ++i) cfma(sacc, cconj(hv[i]), A[i * m + j]);
-                for (int i = k + 1; i < m; ++i) A[i * m + j] = csub(A[i * m + j], cscale(cmul(hv[i], sacc), 2.0));
-            }
-            __syncwarp();
-            // A <- A (I - 2 v v^H) ; Z <- Z (I - 2 v v^H)
-            for (int i = lane; i < m; i += 32) {
-                cplx sa = cmake(0.0, 0.0), sz = cmake(0.0, 0.0);
-                for (int j = k + 1; j < m; ++j) { cfma(sa, A[i * m + j], hv[j]); cfma(sz, Z[i * m + j], hv[j]); }
-                for (int j = k + 1; j < m; ++j) {
-                    A[i * m + j] = csub(A[i * m + j], cscale(cmul(sa, cconj(hv[j])), 2.0));
-                    Z[i * m + j] = csub(Z[i * m + j], cscale(cmul(sz, cconj(hv[j])), 2.0));
-                }
-            }
-            __syncwarp();
-            for (int i = k + 2 + lane; i < m; i += 32) A[i * m + k] = cmake(0.0, 0.0);
-            __syncwarp();
-        }
-    }
-
-    // 2. shifted QR to complex Schur form
-    int hi = m - 1, iter = 0, total = 0, stalled = 0;
-    const int max_total = 30 * m;
-    while (hi > 0) {
-        if (total >= max_total) { stalled = 1; break; }
-        int l = hi;
-        while (l > 0) {
-            double sub = cabsd(A[l * m + l - 1]);
-            double dg = cabsd(A[l * m + l]) + cabsd(A[(l - 1) * m + l - 1]);
-            if (sub <= eps * dg || sub < 1e-300) break;
-            --l;
-        }
-        __syncwarp();
-        if (l > 0 && lane == 0) A[l * m + l - 1] = cmake(0.0, 0.0);
-        __syncwarp();
-        if (l == hi) { --hi; iter = 0; continue; }
-        cplx mu;
-        cplx d = A[hi * m + hi];
-        if (iter == 10 || iter == 20) {
-            double s = fabs(A[hi * m + hi - 1].x) + fabs(A[hi * m + hi - 1].y);
-            mu = cadd(d, cmake(0.75 * s, 0.0));
-        } else {
-            cplx a = A[(hi - 1) * m + hi - 1], b = A[(hi - 1) * m + hi], c = A[hi * m + hi - 1];
-            cplx half = cscale(csub(a, d), 0.5);
-            cplx disc = csqrt_d(cadd(cmul(half, half), cmul(b, c)));
-            cplx mid = cscale(cadd(a, d), 0.5);
-            cplx m1 = cadd(mid, disc), m2 = csub(mid, disc);
-            mu = (cabs2(csub(m1, d)) <= cabs2(csub(m2, d))) ? m1 : m2;
-        }
-        for (int k = l; k < hi; ++k) {
-            if (lane == 0) {
-                cplx x, y;
-                if (k == l) { x = csub(A[l * m + l], mu); y = A[(l + 1) * m + l]; }
-                else { x = A[k * m + k - 1]; y = A[(k + 1) * m + k - 1]; }
-                double c; cplx s;
-                givens(x, y, c, s);
-                rot_c = c;
-                rot_s = s;
-            }
-            __syncwarp();
-            const double c = rot_c;
-            const cplx s = rot_s;
-            rot_rows(A, m, k, k == l ? l : k - 1, c, s, lane);
-            __syncwarp();
-            rot_cols(A, m, k, min(k + 2, hi), c, s, lane);
-            rot_cols(Z, m, k, m - 1, c, s, lane);
-            __syncwarp();
-            if (k > l && lane == 0) A[(k + 1) * m + k - 1] = cmake(0.0, 0.0);
-            __syncwarp();
-        }
-        ++iter;
-        ++total;
-    }
-    __syncwarp();
-
-    // 3. reorder: the nsel best eigenvalues (by key) to the leading positions
-    if (order != 0) {
-        for (int pos = 0; pos < nsel && pos < m; ++pos) {
-            int bi = pos;
-            double bk = order_key(A[pos * m + pos], order);
-            for (int i = pos + 1; i < m; ++i) {
-                double ki = order_key(A[i * m + i], order);
-                if (ki > bk + 1e-14 * fabs(bk)) { bk = ki; bi = i; }
-            }
-            for (int k = bi - 1; k >= pos; --k) {
-                if (lane == 0) {
-                    cplx t11 = A[k * m + k], t22 = A[(k + 1) * m + k + 1];
-                    double c; cplx s;
-                    givens(A[k * m + k + 1], csub(t22, t11), c, s);
-                    rot_c = c;
-                    rot_s = s;
-                }
-                __syncwarp();
-                const double c = rot_c;
-                const cplx s = rot_s;
-                rot_rows(A, m, k, k, c, s, lane);
-                __syncwarp();
-                rot_cols(A, m, k, k + 1, c, s, lane);
-                rot_cols(Z, m, k, m - 1, c, s, lane);
-                __syncwarp();
-                if (lane == 0) A[(k + 1) * m + k] = cmake(0.0, 0.0);
-                __syncwarp();
-            }
-        }
-    }
-
-    // 4. eigenvectors of the triangular factor, then y_p = Z v_p
-    double tnorm = 0.0;
-    for (int e = 0; e < m * m; ++e) tnorm = fmax(tnorm, cabsd(A[e]));
-    const double small = fmax(eps * tnorm, 1e-300);
-    for (int p = lane; p < m; p += 32) {
-        cplx* v = Vt + p * m;
-        for (int i = 0; i < m; ++i) v[i] = cmake(0.0, 0.0);
-        v[p] = cmake(1.0, 0.0);
-        cplx lp = A[p * m + p];
-        for (int i = p - 1; i >= 0; --i) {
-            cplx acc = cmake(0.0, 0.0);
-            for (int j = i + 1; j <= p; ++j) cfma(acc, A[i * m + j], v[j]);
-            cplx den = csub(A[i * m + i], lp);
-            if (cabsd(den) < small) den = cmake(small, 0.0);
-            v[i] = cscale(cdiv(acc, den), -1.0);
-        }
-    }
-    __syncwarp();
-    for (int p = 0; p < m; ++p) {
-        const cplx* v = Vt + p * m;
-        double nrm = 0.0;
-        cplx yv[2];
-        for (int t = 0; t < 2; ++t) {
-            int r = lane + 32 * t;
-            cplx acc = cmake(0.0, 0.0);
-            if (r < m)
-                for (int i = 0; i <= p; ++i) cfma(acc, Z[r * m + i], v[i]);
-            yv[t] = acc;
-            nrm += cabs2(acc);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
-        double inv = nrm > 0.0 ? 1.0 / sqrt(nrm) : 0.0;
-        for (int t = 0; t < 2; ++t) {
-            int r = lane + 32 * t;
-            if (r < m) evecs[(long long)p * m + r] = cscale(yv[t], inv);
-        }
-        if (lane == 0) evals[p] = A[p * m + p];
-    }
-    if (Tout)
-        for (int e = lane; e < m * m; e += 32) { int i = e / m, j = e % m; Tout[(long long)j * m + i] = A[e]; }
-    if (Zout)
-        for (int e = lane; e < m * m; e += 32) { int i = e / m, j = e % m; Zout[(long long)j * m + i] = Z[e]; }
-    if (lane == 0) info[0] = stalled;
+    small_schur_warp(Ain, lda, m, hess_in, order, nsel, evals, evecs, Tout, Zout, info, A, Z, Vt, hv, rot_s, rot_c);
 }
 
 }  // namespace

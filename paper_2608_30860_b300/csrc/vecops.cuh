@@ -40,3 +40,4 @@ int trisylv_f64(const cplx* T, cplx* X, int n, cplx s, cudaStream_t st);
 // (column-major, ld m; nullable).
 int small_schur(const cplx* A, int lda, int m, int hess_in, int order, int nsel, cplx* evals, cplx* evecs,
                 cplx* Tout, cplx* Zout, int* info, cudaStream_t s);
+
