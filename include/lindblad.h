@@ -188,6 +188,40 @@ lb_status steady_state_adjoint(lindblad_handle h, const void* rho_dev, const voi
                                void* gH_dev, void* gL_dev, const lb_opts* opts, lb_info* info,
                                void* stream);
 
+/* Batched steady states of `count` independent Lindbladians of uneven size sharing the number of
+ * jumps d (a parameter sweep), each by Alg. 4 with complex64 contractions and an FP64 anchor, all
+ * instances in one set-up launch and one persistent solve launch (a work queue taken in
+ * decreasing n), replayed as one CUDA graph on a private stream ordered after `stream`.
+ * Per instance: G = -iH - 1/2 sum_j L_j^dag L_j and its complex Schur form G = Q T Q^dag
+ * computed on the device in FP64 (Householder-Hessenberg + shifted QR); Phi-Arnoldi cycles of
+ * length opts->krylov_m (clipped to [8, 32]) that carry the 5 Schur vectors next nearest 1 across
+ * a restart, first in complex64 while the Ritz residual falls, then anchored in FP64: the iterate
+ * rho~ = S~^{-1} xi and its image Phi(S~ rho~) = -K~ rho~ are formed in FP64 and every complex64
+ * basis vector is used exactly orthogonal to it, so rounding only touches the correction; at
+ * most opts->max_restarts cycles per phase, until ||L(rho)||_max < opts->tol in the original
+ * basis.  opts->precision, eta and the GMRES / refinement fields are not used.
+ *   n        : host array of count sizes, each 2 <= n_i <= 256.
+ *   H_dev    : the count Hamiltonians packed back to back (device, complex128, row-major,
+ *              instance i at offset sum_{k<i} n_k^2 elements).
+ *   L_dev    : the jumps, instance i's d stacked n_i x n_i matrices at offset d sum_{k<i} n_k^2.
+ *   rho_dev  : output, packed like H_dev (Hermitian, trace 1; written for every instance whose
+ *              set-up status is LB_OK; untouched otherwise).
+ *   workspace: device memory of at least lindblad_batched_workspace_bytes(count, n, d, opts)
+ *              bytes, 256-byte aligned, owned by the caller; nothing in it needs to be zero.
+ *   infos    : nullable host array of count lb_info (status, residual_max, residual_fro of the
+ *              last original-basis residual, phi_applies = complex64 Phi applications,
+ *              restarts = cycles, refine_steps = FP64-anchored cycles, solve_ms = wall time of
+ *              the batch).
+ * Synchronises `stream` before returning.  Returns LB_INVALID_ARG (count < 1, d < 1, a size out
+ * of range, a null pointer), LB_WORKSPACE_TOO_SMALL, LB_CUDA_ERROR, else the first negative
+ * per-instance status (LB_SOLVER_ERROR: the Schur QR iteration stalled), else the first positive
+ * one (LB_NOT_CONVERGED; LB_S_SINGULAR for Theorem 1 case 1, reported without solving), else
+ * LB_OK. */
+size_t lindblad_batched_workspace_bytes(int count, const int* n, int d, const lb_opts* opts);
+lb_status steady_state_batched(int count, const int* n, int d, const void* H_dev, const void* L_dev,
+                               void* rho_dev, void* workspace, size_t ws_bytes, const lb_opts* opts,
+                               lb_info* infos, void* stream);
+
 /* Kernel timing (diagnostics, no effect on results).  While enabled, the library records CUDA
  * events on the launching stream around every tensor-core GEMM launch (kernel id 0) and every
  * FP64 GEMM launch of the residual (kernel id 1).  lb_kernel_stats synchronises the stream and

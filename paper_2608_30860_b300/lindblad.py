@@ -87,6 +87,10 @@ def load_library(path: str = LIB_PATH):
     lib.low_spectrum.restype = i
     lib.steady_state_adjoint.argtypes = [vp, vp, vp, vp, vp, vp, P(LbOpts), P(LbInfo), vp]
     lib.steady_state_adjoint.restype = i
+    lib.lindblad_batched_workspace_bytes.argtypes = [i, P(i), i, P(LbOpts)]
+    lib.lindblad_batched_workspace_bytes.restype = sz
+    lib.steady_state_batched.argtypes = [i, P(i), i, vp, vp, vp, vp, sz, P(LbOpts), P(LbInfo), vp]
+    lib.steady_state_batched.restype = i
     lib.lindblad_destroy.argtypes = [vp]
     lib.lindblad_destroy.restype = None
     lib.lb_set_profiling.argtypes = [vp, i]
@@ -258,6 +262,55 @@ def steady_state_adjoint(h: Handle, rho: torch.Tensor, O: torch.Tensor, opts: Lb
     if st < 0 or st == 2:
         raise LindbladError(st, "steady_state_adjoint")
     return w, gH, gL, info.as_dict(), st
+
+
+def _sizes(ns) -> ctypes.Array:
+    arr = (ctypes.c_int * len(ns))(*[int(v) for v in ns])
+    return arr
+
+
+def lindblad_batched_workspace_bytes(ns, d: int, opts: LbOpts | None = None) -> int:
+    o = opts or default_opts()
+    return int(load_library().lindblad_batched_workspace_bytes(len(ns), _sizes(ns), d, ctypes.byref(o)))
+
+
+def pack_batch(Hs, Ls):
+    """Packs per-instance H (n_i, n_i) and L (d, n_i, n_i) tensors back to back (the batched layout)."""
+    H = torch.cat([h.reshape(-1) for h in Hs]).contiguous()
+    L = torch.cat([l.reshape(-1) for l in Ls]).contiguous()
+    return H, L
+
+
+def unpack_batch(rho: torch.Tensor, ns):
+    out, off = [], 0
+    for n in ns:
+        out.append(rho[off:off + n * n].view(n, n))
+        off += n * n
+    return out
+
+
+def steady_state_batched(ns, d: int, H: torch.Tensor, L: torch.Tensor, opts: LbOpts | None = None,
+                         rho: torch.Tensor | None = None, workspace: torch.Tensor | None = None):
+    """Steady states of len(ns) Lindbladians packed by pack_batch (device complex128).
+    Returns (rho packed, list of info dicts, status); raises on a negative status."""
+    lib = load_library()
+    o = opts or default_opts(krylov_m=32)
+    count = len(ns)
+    total = sum(int(v) * int(v) for v in ns)
+    if H.numel() != total or L.numel() != d * total:
+        raise ValueError("packed H / L sizes do not match ns and d")
+    nbytes = lindblad_batched_workspace_bytes(ns, d, o)
+    if nbytes == 0:
+        raise LindbladError(-1, "lindblad_batched_workspace_bytes")
+    if workspace is None:
+        workspace = torch.empty(nbytes, dtype=torch.uint8, device=H.device)
+    rho = torch.empty(total, dtype=torch.complex128, device=H.device) if rho is None else rho
+    infos = (LbInfo * count)()
+    st = lib.steady_state_batched(count, _sizes(ns), d, _dev(H), _dev(L), _dev(rho, (total,)),
+                                  workspace.data_ptr(), workspace.numel(), ctypes.byref(o), infos, _stream())
+    if st < 0:
+        raise LindbladError(st, "steady_state_batched")
+    return rho, [inf.as_dict() for inf in infos], st
 
 
 def lindblad_destroy(h: Handle):

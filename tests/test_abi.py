@@ -60,3 +60,19 @@ def test_status_strings(lib):
     lib.lb_status_string.restype = ctypes.c_char_p
     assert lib.lb_status_string(-3) == b"LB_ETA_EXCLUDED"
     assert lib.lb_status_string(2) == b"LB_S_SINGULAR"
+
+
+def test_batched_workspace_query_host_logic():
+    """Workspace sizing of the batched engine is host arithmetic: positive and growing with the
+    sizes, zero for a size outside [2, 256] or an empty batch."""
+    import ctypes
+
+    import paper_2608_30860_b300 as B
+    small = B.lindblad_batched_workspace_bytes([16, 40], 2)
+    big = B.lindblad_batched_workspace_bytes([16, 40, 160], 2)
+    assert 0 < small < big
+    assert big % 256 == 0
+    assert B.lindblad_batched_workspace_bytes([16, 257], 2) == 0
+    assert B.lindblad_batched_workspace_bytes([1], 2) == 0
+    lib = B.load_library()
+    assert lib.lindblad_batched_workspace_bytes(0, (ctypes.c_int * 1)(16), 2, None) == 0
