@@ -68,18 +68,31 @@ template <typename C> __device__ __forceinline__ C cdv(C a, C b) {
     const double2 q = cdiv(make_double2(a.x, a.y), make_double2(b.x, b.y));
     return cm<C>(q.x, q.y);
 }
+// complex64 division kept in FP32 (FP64 instructions are scarce on this part)
+template <> __device__ __forceinline__ float2 cdv<float2>(float2 a, float2 b) {
+    const float inv = 1.f / (b.x * b.x + b.y * b.y);
+    return make_float2((a.x * b.x + a.y * b.y) * inv, (a.y * b.x - a.x * b.y) * inv);
+}
+template <typename C> __device__ __forceinline__ C mk(typename Real<C>::T a, typename Real<C>::T b) {
+    C r;
+    r.x = a;
+    r.y = b;
+    return r;
+}
 
 // ------------------------------------------------------------------ CTA-level building blocks
 // C = alpha op(A) op(B) + beta C  (n x n row-major; op 0 = N, 2 = conjugate transpose);
-// sa, sb: GT x (GT+1) shared tiles.  C must not alias A or B.
+// sa, sb: GT x (GT+1) shared tiles.  C must not alias A or B.  Structure flags: a_upper -- op(A)
+// is upper triangular (k-tiles left of the row tile are skipped); upper_only -- only tiles on or
+// above the diagonal are formed (the caller mirrors a Hermitian result).
 template <typename C>
 __device__ void cta_gemm(const C* A, int opA, const C* B, int opB, C* Cm, int n, C alpha, C beta, int use_beta,
-                         C* sa, C* sb) {
+                         C* sa, C* sb, int a_upper = 0, int upper_only = 0) {
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 8 x 32
     for (int r0 = 0; r0 < n; r0 += GT) {
-        for (int c0 = 0; c0 < n; c0 += GT) {
+        for (int c0 = upper_only ? r0 : 0; c0 < n; c0 += GT) {
             C acc[4] = {cz<C>(), cz<C>(), cz<C>(), cz<C>()};
-            for (int k0 = 0; k0 < n; k0 += GT) {
+            for (int k0 = a_upper ? r0 : 0; k0 < n; k0 += GT) {
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     const int rr = ty + 8 * i;
@@ -162,42 +175,106 @@ __device__ double2 cta_trace(const C* X, int n, double* red) {
     return cta_sum2(re, im, red);
 }
 
-// anti-diagonal left-looking triangular Lyapunov solve (T - s) X + X (T - s)^dag = C, in place
+// Blocked solve of the triangular Lyapunov equation (T - s) X + X (T - s)^dag = C, in place.
+// 32 x 32 blocks (I, J) in decreasing I + J: each block first subtracts the solved coupling
+// sum_{K>I} T_IK X_KJ + sum_{K>J} X_IK T_JK^dag (shared-memory tiles, 4 outputs per thread), then
+// solves its leaf T_II Y + Y T_JJ^dag = C_IJ in shared memory by anti-diagonals, 8 threads per
+// entry.  sa, sb, sc: GT x (GT + 1) shared tiles; entries beyond n are held at zero.
 template <typename C>
-__device__ void cta_trisylv(const C* T, C* X, int n, double s) {
+__device__ void cta_trisylv(const C* T, C* X, int n, double s, C* sa, C* sb, C* sc) {
     typedef typename Real<C>::T R;
-    const int t4 = threadIdx.x & 3, slot = threadIdx.x >> 2;
-    for (int S = 2 * n - 2; S >= 0; --S) {
-        const int alo = max(0, S - (n - 1)), cnt = min(S, n - 1) - alo + 1;
-        for (int base = 0; base < cnt; base += BT / 4) {
-            const int e = base + slot;
-            const bool valid = e < cnt;
-            const int a = alo + e, b = S - a;
-            R ax = 0, ay = 0;
-            if (valid) {
-                for (int r = a + 1 + t4; r < n; r += 4) {
-                    const C m = T[(long long)a * n + r], x = X[(long long)r * n + b];
-                    ax += m.x * x.x - m.y * x.y;
-                    ay += m.x * x.y + m.y * x.x;
+    constexpr int P = GT + 1;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int slot = threadIdx.x >> 3, t8 = threadIdx.x & 7;
+    const int nb = (n + GT - 1) / GT;
+    const R shift2 = (R)(2.0 * s);
+    for (int S = 2 * nb - 2; S >= 0; --S) {
+        const int Ilo = max(0, S - (nb - 1)), Ihi = min(S, nb - 1);
+        for (int I = Ilo; I <= Ihi; ++I) {
+            const int J = S - I;
+            const int r0 = I * GT, c0 = J * GT;
+            C acc[4] = {cz<C>(), cz<C>(), cz<C>(), cz<C>()};
+            // T[I rows, k] X[k, J cols] over k >= (I + 1) GT
+            for (int k0 = r0 + GT; k0 < n; k0 += GT) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int rr = ty + 8 * i;
+                    sa[rr * P + tx] = (r0 + rr < n && k0 + tx < n) ? T[(long long)(r0 + rr) * n + k0 + tx] : cz<C>();
+                    sb[rr * P + tx] = (k0 + rr < n && c0 + tx < n) ? X[(long long)(k0 + rr) * n + c0 + tx] : cz<C>();
                 }
-                for (int r = b + 1 + t4; r < n; r += 4) {
-                    const C x = X[(long long)a * n + r], m = T[(long long)b * n + r];
-                    ax += x.x * m.x + x.y * m.y;
-                    ay += x.y * m.x - x.x * m.y;
+                __syncthreads();
+#pragma unroll 8
+                for (int k = 0; k < GT; ++k) {
+                    const C bv = sb[k * P + tx];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) cf(acc[i], sa[(ty + 8 * i) * P + k], bv);
                 }
+                __syncthreads();
             }
-            ax += __shfl_xor_sync(0xffffffffu, ax, 1);
-            ay += __shfl_xor_sync(0xffffffffu, ay, 1);
-            ax += __shfl_xor_sync(0xffffffffu, ax, 2);
-            ay += __shfl_xor_sync(0xffffffffu, ay, 2);
-            if (valid && t4 == 0) {
-                const C ta = T[(long long)a * n + a], tb = T[(long long)b * n + b];
-                const C den = cm<C>((double)ta.x + (double)tb.x - 2.0 * s, (double)ta.y - (double)tb.y);
-                const C v = cs(X[(long long)a * n + b], cm<C>(ax, ay));
-                X[(long long)a * n + b] = cdv(v, den);
+            // X[I rows, k] T[J rows, k]^dag over k >= (J + 1) GT
+            for (int k0 = c0 + GT; k0 < n; k0 += GT) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int rr = ty + 8 * i;
+                    sa[rr * P + tx] = (r0 + rr < n && k0 + tx < n) ? X[(long long)(r0 + rr) * n + k0 + tx] : cz<C>();
+                    // sb[k][j] = conj(T[c0 + j, k0 + k]) (coalesced load, transposed store)
+                    sb[tx * P + rr] = (c0 + rr < n && k0 + tx < n) ? cc(T[(long long)(c0 + rr) * n + k0 + tx]) : cz<C>();
+                }
+                __syncthreads();
+#pragma unroll 8
+                for (int k = 0; k < GT; ++k) {
+                    const C bv = sb[k * P + tx];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) cf(acc[i], sa[(ty + 8 * i) * P + k], bv);
+                }
+                __syncthreads();
             }
+            // leaf right-hand side and diagonal blocks
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int rr = ty + 8 * i;
+                const bool in = r0 + rr < n && c0 + tx < n;
+                sc[rr * P + tx] = in ? cs(X[(long long)(r0 + rr) * n + c0 + tx], acc[i]) : cz<C>();
+                sa[rr * P + tx] = (r0 + rr < n && r0 + tx < n) ? T[(long long)(r0 + rr) * n + r0 + tx] : cz<C>();
+                sb[rr * P + tx] = (c0 + rr < n && c0 + tx < n) ? T[(long long)(c0 + rr) * n + c0 + tx] : cz<C>();
+            }
+            __syncthreads();
+            for (int d = 2 * GT - 2; d >= 0; --d) {
+                const int alo = max(0, d - (GT - 1)), cnt = min(d, GT - 1) - alo + 1;
+                const bool valid = slot < cnt;
+                const int a = alo + slot, b = d - a;
+                R ax = 0, ay = 0;
+                if (valid) {
+                    for (int r = a + 1 + t8; r < GT; r += 8) {
+                        const C m = sa[a * P + r], x = sc[r * P + b];
+                        ax += m.x * x.x - m.y * x.y;
+                        ay += m.x * x.y + m.y * x.x;
+                    }
+                    for (int r = b + 1 + t8; r < GT; r += 8) {
+                        const C x = sc[a * P + r], m = sb[b * P + r];
+                        ax += x.x * m.x + x.y * m.y;
+                        ay += x.y * m.x - x.x * m.y;
+                    }
+                }
+#pragma unroll
+                for (int o = 1; o < 8; o <<= 1) {
+                    ax += __shfl_xor_sync(0xffffffffu, ax, o);
+                    ay += __shfl_xor_sync(0xffffffffu, ay, o);
+                }
+                if (valid && t8 == 0 && r0 + a < n && c0 + b < n) {
+                    const C ta = sa[a * P + a], tb = sb[b * P + b];
+                    const C den = mk<C>(ta.x + tb.x - shift2, ta.y - tb.y);
+                    sc[a * P + b] = cdv(cs(sc[a * P + b], mk<C>(ax, ay)), den);
+                }
+                __syncthreads();
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int rr = ty + 8 * i;
+                if (r0 + rr < n && c0 + tx < n) X[(long long)(r0 + rr) * n + c0 + tx] = sc[rr * P + tx];
+            }
+            __syncthreads();
         }
-        __syncthreads();
     }
 }
 
@@ -379,11 +456,14 @@ __device__ View make_view(const Inst& in, int d, cplx* a64, float2* a32) {
 struct Shared {
     cplx ga[GT * (GT + 1)];
     cplx gb[GT * (GT + 1)];
+    cplx gc[GT * (GT + 1)];
     double red[64];
     cplx hm[(MB + 1) * MB];      // projected matrix V^dag Phi V, column-major, ld MB + 1
-    cplx ssA[MB * MB], ssZ[MB * MB], ssV[MB * MB];
-    cplx ev[MB], evec[MB * MB], zs[MB * MB], hvv[MB + 1];
+    cplx ssA[MB * (MB + 1)], ssZ[MB * (MB + 1)], ssV[MB * (MB + 1)];
+    cplx ev[MB], zs[MB * MB], hvv[MB + 1];
     cplx hb[MB + 1];             // block dot products
+    float2 hbf[MB + 1];          // the same in FP32
+    float2 zsf[MB * MB];         // carried Schur vectors' coefficients in FP32
     cplx alpha[MB + 1];          // <v0, V_i> in FP64 (v0 the FP64 anchor, V_i the stored complex64 vector)
     double nu[MB + 1];           // || V_i - alpha_i v0 ||
     cplx shc[4];
@@ -408,7 +488,8 @@ __device__ void phi32(const View& v, const float2* x, float2* w, Shared& sm) {
     const long long nn = (long long)v.n * v.n;
     for (long long e = threadIdx.x; e < nn; e += BT) v.Z1[e] = x[e];
     __syncthreads();
-    cta_trisylv(v.Tf, v.Z1, v.n, 0.0);
+    cta_trisylv(v.Tf, v.Z1, v.n, 0.0, reinterpret_cast<float2*>(sm.ga), reinterpret_cast<float2*>(sm.gb),
+                reinterpret_cast<float2*>(sm.gc));
     jump32(v, v.Z1, w, -1.f, sm);
 }
 
@@ -428,9 +509,19 @@ __device__ void multidot32(const float2* V, long long nn, int cnt, const float2*
             re += __shfl_xor_sync(0xffffffffu, re, o);
             im += __shfl_xor_sync(0xffffffffu, im, o);
         }
-        if (lane == 0) sm.hb[i] = cmake(re, im);
+        if (lane == 0) {
+            sm.hb[i] = cmake(re, im);
+            sm.hbf[i] = make_float2(re, im);
+        }
     }
     __syncthreads();
+}
+
+// ||x||^2 of a complex64 vector (FP32 partial sums per thread, CTA reduction in FP64)
+__device__ double norm2_32(const float2* x, long long nn, Shared& sm) {
+    float acc = 0.f;
+    for (long long e = threadIdx.x; e < nn; e += BT) acc = fmaf(x[e].x, x[e].x, fmaf(x[e].y, x[e].y, acc));
+    return cta_sum2((double)acc, 0.0, sm.red).x;
 }
 
 // w <- w - sum_{i<cnt} hb[i] V_i (complex64)
@@ -439,9 +530,9 @@ __device__ void multiaxpy32(const float2* V, long long nn, int cnt, float2* w, c
         float2 acc = w[e];
         for (int i = 0; i < cnt; ++i) {
             const float2 a = V[i * nn + e];
-            const float hx = (float)sm.hb[i].x, hy = (float)sm.hb[i].y;
-            acc.x -= hx * a.x - hy * a.y;
-            acc.y -= hx * a.y + hy * a.x;
+            const float2 h = sm.hbf[i];
+            acc.x -= h.x * a.x - h.y * a.y;
+            acc.y -= h.x * a.y + h.y * a.x;
         }
         w[e] = acc;
     }
@@ -482,6 +573,17 @@ __device__ void herm_normalize(cplx* X, cplx* tmp, int n, double* red) {
     __syncthreads();
     tr = cta_trace(X, n, red);
     for (long long e = threadIdx.x; e < nn; e += BT) X[e] = cscale(X[e], 1.0 / tr.x);
+    __syncthreads();
+}
+
+// lower triangle of a Hermitian matrix from its upper triangle
+template <typename C>
+__device__ void mirror_lower(C* X, int n) {
+    const long long nn = (long long)n * n;
+    for (long long e = threadIdx.x; e < nn; e += BT) {
+        const long long i = e / n, j = e % n;
+        if (i > j) X[e] = cc(X[j * n + i]);
+    }
     __syncthreads();
 }
 
@@ -562,7 +664,7 @@ __device__ double aug_cycle(const View& v, int m, int& nU, int& applies, Shared&
             multidot32(v.V, nn, q, x, sm);
             multiaxpy32(v.V, nn, q, x, sm);
         }
-        const double xn = sqrt(fmax(cta_dot(x, x, nn, sm.red).x, 0.0));
+        const double xn = sqrt(fmax(norm2_32(x, nn, sm), 0.0));
         if (!(xn > 1e-3)) continue;
         for (long long e = threadIdx.x; e < nn; e += BT) { x[e].x /= (float)xn; x[e].y /= (float)xn; }
         __syncthreads();
@@ -625,7 +727,7 @@ __device__ double aug_cycle(const View& v, int m, int& nU, int& applies, Shared&
             float2* w = v.V + (j + 1) * nn;
             phi32(v, v.V + j * nn, w, sm);
             ++applies;
-            const double wn = sqrt(fmax(cta_dot(w, w, nn, sm.red).x, 0.0));
+            const double wn = sqrt(fmax(norm2_32(w, nn, sm), 0.0));
             for (int pass = 0; pass < 2; ++pass) {
                 multidot32(v.V, nn, j + 1, w, sm);
                 multiaxpy32(v.V, nn, j + 1, w, sm);
@@ -633,7 +735,7 @@ __device__ double aug_cycle(const View& v, int m, int& nU, int& applies, Shared&
                     for (int i = 0; i <= j; ++i) sm.hm[j * (MB + 1) + i] = cadd(sm.hm[j * (MB + 1) + i], sm.hb[i]);
                 __syncthreads();
             }
-            const double beta = sqrt(fmax(cta_dot(w, w, nn, sm.red).x, 0.0));
+            const double beta = sqrt(fmax(norm2_32(w, nn, sm), 0.0));
             if (threadIdx.x == 0) sm.hm[j * (MB + 1) + j + 1] = cmake(beta, 0.0);
             __syncthreads();
             if (!(beta > 1e-6 * wn) || j + 1 == m) break;
@@ -652,7 +754,7 @@ __device__ double aug_cycle(const View& v, int m, int& nU, int& applies, Shared&
     }
     // ordered Schur form of the kk x kk projected matrix
     if (threadIdx.x < 32)
-        small_schur_warp(sm.hm, MB + 1, kk, 0, 2, PK < kk ? PK : kk, sm.ev, sm.evec, nullptr, sm.zs, nullptr, sm.ssA,
+        small_schur_warp(sm.hm, MB + 1, kk, 0, 2, PK < kk ? PK : kk, sm.ev, nullptr, nullptr, sm.zs, nullptr, sm.ssA,
                          sm.ssZ, sm.ssV, sm.hvv, sm.shc[2], sm.shd[2]);
     __syncthreads();
     const int npk = PK < kk ? PK : kk;
@@ -695,14 +797,16 @@ __device__ double aug_cycle(const View& v, int m, int& nU, int& applies, Shared&
     for (long long e = threadIdx.x; e < nn; e += BT) xi[e] = cdiv(xi[e], tr);
     // carried Schur vectors 1 .. npk-1 (complex64)
     nU = npk - 1;
+    for (int e = threadIdx.x; e < npk * kk; e += BT) sm.zsf[e] = make_float2((float)sm.zs[e].x, (float)sm.zs[e].y);
+    __syncthreads();
     for (long long e = threadIdx.x; e < nn; e += BT) {
         for (int s = 1; s < npk; ++s) {
             float ax = 0.f, ay = 0.f;
             for (int t = 0; t < kk; ++t) {
                 const float2 x = v.V[t * nn + e];
-                const float zx = (float)sm.zs[s * kk + t].x, zy = (float)sm.zs[s * kk + t].y;
-                ax += zx * x.x - zy * x.y;
-                ay += zx * x.y + zy * x.x;
+                const float2 z = sm.zsf[s * kk + t];
+                ax += z.x * x.x - z.y * x.y;
+                ay += z.x * x.y + z.y * x.x;
             }
             v.Ub[(s - 1) * nn + e] = make_float2(ax, ay);
         }
@@ -773,18 +877,19 @@ k_batched_solve(const Inst* __restrict__ insts, const int* __restrict__ order, i
             ++anchors;
             for (long long e = threadIdx.x; e < nn; e += BT) rt[e] = xi[e];
             __syncthreads();
-            cta_trisylv(v.T, rt, n, 0.0);
+            cta_trisylv(v.T, rt, n, 0.0, sm.ga, sm.gb, sm.gc);
             herm_normalize(rt, v.S3, n, sm.red);
             // S4 = T rho~ + rho~ T^dag, S5 = K~ rho~, Schur-coordinate residual S4 + S5
-            cta_gemm(v.T, 0, rt, 0, v.S3, n, cmake(1, 0), cmake(0, 0), 0, sm.ga, sm.gb);
+            cta_gemm(v.T, 0, rt, 0, v.S3, n, cmake(1, 0), cmake(0, 0), 0, sm.ga, sm.gb, 1, 0);
             for (long long e = threadIdx.x; e < nn; e += BT) {
                 const long long i = e / n, j = e % n;
                 v.S4[e] = cadd(v.S3[e], cconj(v.S3[j * n + i]));
             }
             for (int j = 0; j < d; ++j) {
                 cta_gemm(v.Lt + j * nn, 0, rt, 0, v.S3, n, cmake(1, 0), cmake(0, 0), 0, sm.ga, sm.gb);
-                cta_gemm(v.S3, 0, v.Lt + j * nn, 2, v.S5, n, cmake(1, 0), cmake(1, 0), j > 0, sm.ga, sm.gb);
+                cta_gemm(v.S3, 0, v.Lt + j * nn, 2, v.S5, n, cmake(1, 0), cmake(1, 0), j > 0, sm.ga, sm.gb, 0, 1);
             }
+            mirror_lower(v.S5, n);
             double mx = 0.0;
             for (long long e = threadIdx.x; e < nn; e += BT) mx = fmax(mx, cabs2(cadd(v.S4[e], v.S5[e])));
             const double rs_max = sqrt(cta_max(mx, sm.red));
@@ -793,12 +898,18 @@ k_batched_solve(const Inst* __restrict__ insts, const int* __restrict__ order, i
                 cta_gemm(v.Q, 0, rt, 0, v.S3, n, cmake(1, 0), cmake(0, 0), 0, sm.ga, sm.gb);
                 cta_gemm(v.S3, 0, v.Q, 2, rho, n, cmake(1, 0), cmake(0, 0), 0, sm.ga, sm.gb);
                 herm_normalize(rho, v.S3, n, sm.red);
-                cta_gemm(v.G, 0, rho, 0, v.S3, n, cmake(1, 0), cmake(0, 0), 0, sm.ga, sm.gb);
-                cta_gemm(rho, 0, v.G, 2, v.S3, n, cmake(1, 0), cmake(1, 0), 1, sm.ga, sm.gb);
+                // L(rho) = G rho + (G rho)^dag + sum_j L_j rho L_j^dag (rho Hermitian; upper triangle, mirrored)
+                cta_gemm(v.G, 0, rho, 0, v.S6, n, cmake(1, 0), cmake(0, 0), 0, sm.ga, sm.gb);
+                for (long long e = threadIdx.x; e < nn; e += BT) {
+                    const long long i = e / n, j = e % n;
+                    v.S3[e] = cadd(v.S6[e], cconj(v.S6[j * n + i]));
+                }
+                __syncthreads();
                 for (int j = 0; j < d; ++j) {
                     cta_gemm(L + j * nn, 0, rho, 0, v.S6, n, cmake(1, 0), cmake(0, 0), 0, sm.ga, sm.gb);
-                    cta_gemm(v.S6, 0, L + j * nn, 2, v.S3, n, cmake(1, 0), cmake(1, 0), 1, sm.ga, sm.gb);
+                    cta_gemm(v.S6, 0, L + j * nn, 2, v.S3, n, cmake(1, 0), cmake(1, 0), 1, sm.ga, sm.gb, 0, 1);
                 }
+                mirror_lower(v.S3, n);
                 double m2 = 0.0, s2 = 0.0;
                 for (long long e = threadIdx.x; e < nn; e += BT) {
                     const double a2 = cabs2(v.S3[e]);

@@ -23,9 +23,9 @@ __global__ void k_small_schur(const cplx* __restrict__ Ain, int lda, int m, int 
                               cplx* __restrict__ evals, cplx* __restrict__ evecs, cplx* __restrict__ Tout,
                               cplx* __restrict__ Zout, int* info) {
     extern __shared__ __align__(16) unsigned char hsm[];
-    cplx* A = reinterpret_cast<cplx*>(hsm);   // m x m row-major
-    cplx* Z = A + m * m;                        // m x m row-major
-    cplx* Vt = Z + m * m;                       // m x m (eigenvectors of T, row p = vector p)
+    cplx* A = reinterpret_cast<cplx*>(hsm);   // m x m row-major, row stride m + 1
+    cplx* Z = A + m * (m + 1);                  // m x m row-major, row stride m + 1
+    cplx* Vt = Z + m * (m + 1);                 // eigenvectors of T, row p = vector p, stride m + 1
     __shared__ cplx hv[64];
     __shared__ cplx rot_s;
     __shared__ double rot_c;
@@ -37,11 +37,11 @@ __global__ void k_small_schur(const cplx* __restrict__ Ain, int lda, int m, int 
 int small_schur(const cplx* A, int lda, int m, int hess_in, int order, int nsel, cplx* evals, cplx* evecs,
                 cplx* Tout, cplx* Zout, int* info, cudaStream_t s) {
     if (m < 1 || m > 64) return -1;
-    size_t smem = 3 * (size_t)m * m * sizeof(cplx);
+    size_t smem = 3 * (size_t)m * (m + 1) * sizeof(cplx);
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_small_schur, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             3 * 64 * 64 * (int)sizeof(cplx));
+                             3 * 64 * 65 * (int)sizeof(cplx));
         attr = true;
     }
     k_small_schur<<<1, 32, smem, s>>>(A, lda, m, hess_in, order, nsel, evals, evecs, Tout, Zout, info); lb_note_launch();
