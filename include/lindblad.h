@@ -222,6 +222,28 @@ lb_status steady_state_batched(int count, const int* n, int d, const void* H_dev
                                void* rho_dev, void* workspace, size_t ws_bytes, const lb_opts* opts,
                                lb_info* infos, void* stream);
 
+/* Largest n accepted by lindbladian_apply_noalloc (its scratch is sized for it). */
+#define LB_NOALLOC_NMAX 512
+
+/* R = L(X) = G X + X G^dag + sum_j L_j X L_j^dag in FP64, original basis, straight from H and
+ * the jumps: the same result as lindbladian_apply (up to rounding order) but with no handle, no
+ * caller workspace and no device allocation of any kind.  The paper has no counterpart: this is
+ * plumbing for callers that must not allocate -- a residual monitor inside a latency-bound
+ * loop, where cudaMalloc would synchronise the device and stall the other streams, or a process
+ * that has already handed all device memory to its own buffers and holds no set-up workspace.
+ *   H_dev : n x n Hamiltonian; L_dev : d stacked n x n jumps; X_dev : n x n input; R_dev : n x n
+ *           output (all device, complex128, row-major; R must not alias the inputs).
+ * Scratch: two n x n complex128 matrices in a file-scope device array of
+ * 2 * LB_NOALLOC_NMAX^2 * 16 bytes (8 MiB) that belongs to the library module; every scratch
+ * element is written before it is read, so nothing has to start at zero.  The first call on
+ * each device looks the array up with cudaGetSymbolAddress (which may load the module); make
+ * that first call before any stream capture is begun.  Calls on one device share the array:
+ * calls that overlap in time (other streams, other host threads) race, so serialise them.
+ * Stream-ordered, no host synchronisation.  Errors: LB_INVALID_ARG (null pointer, n < 2,
+ * d < 1), LB_WORKSPACE_TOO_SMALL (n > LB_NOALLOC_NMAX), LB_CUDA_ERROR. */
+lb_status lindbladian_apply_noalloc(const void* H_dev, const void* L_dev, int n, int d, const void* X_dev,
+                                    void* R_dev, void* stream);
+
 /* Kernel timing (diagnostics, no effect on results).  While enabled, the library records CUDA
  * events on the launching stream around every tensor-core GEMM launch (kernel id 0) and every
  * FP64 GEMM launch of the residual (kernel id 1).  lb_kernel_stats synchronises the stream and

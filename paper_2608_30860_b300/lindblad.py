@@ -91,6 +91,8 @@ def load_library(path: str = LIB_PATH):
     lib.lindblad_batched_workspace_bytes.restype = sz
     lib.steady_state_batched.argtypes = [i, P(i), i, vp, vp, vp, vp, sz, P(LbOpts), P(LbInfo), vp]
     lib.steady_state_batched.restype = i
+    lib.lindbladian_apply_noalloc.argtypes = [vp, vp, i, i, vp, vp, vp]
+    lib.lindbladian_apply_noalloc.restype = i
     lib.lindblad_destroy.argtypes = [vp]
     lib.lindblad_destroy.restype = None
     lib.lb_set_profiling.argtypes = [vp, i]
@@ -311,6 +313,18 @@ def steady_state_batched(ns, d: int, H: torch.Tensor, L: torch.Tensor, opts: LbO
     if st < 0:
         raise LindbladError(st, "steady_state_batched")
     return rho, [inf.as_dict() for inf in infos], st
+
+
+def lindbladian_apply_noalloc(H: torch.Tensor, L: torch.Tensor, X: torch.Tensor,
+                              R: torch.Tensor | None = None) -> torch.Tensor:
+    """R = L(X) from H (n, n) and L (d, n, n) without a handle or workspace (n <= 512)."""
+    n, d = H.shape[0], L.shape[0]
+    R = torch.empty_like(X) if R is None else R
+    st = load_library().lindbladian_apply_noalloc(_dev(H, (n, n)), _dev(L, (d, n, n)), n, d, _dev(X, (n, n)),
+                                                  _dev(R, (n, n)), _stream())
+    if st != 0:
+        raise LindbladError(st, "lindbladian_apply_noalloc")
+    return R
 
 
 def lindblad_destroy(h: Handle):
