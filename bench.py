@@ -7,6 +7,7 @@ term as two tcgen05 split-FP16 GEMMs.  Inputs are synthetic (seeded), already re
 the operands (L~ planes, 1.6 GB) exceed the 126 MB L2, so no flush is needed between steps.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--solve]
+python bench.py --workload sweep   # the batched sweep: 1024 Kerr-cat steady states of uneven n
 Multi-GPU: replicas only (each rank runs its own copy of the workload; weak scaling).
 """
 from __future__ import annotations
@@ -119,6 +120,133 @@ def cpu_baseline(n_sites=12, d_sample=1):
                        f"est. {per_apply:.1f} s per apply")}
 
 
+SWEEP = dict(workload="kerr_cat_sweep_1024", count=1024, seed=0, n_range=[16, 160], d=2,
+             eps2=[1.0, 8.0], K=[0.5, 2.0], kappa1=[1e-3, 1e-1], kappa2=1.0)
+
+
+def fp32_alu_peak_tflops():
+    """FP32 CUDA-core peak from the part's unit counts: 148 SMs x 128 FMA/clk x 2 flops x 2.032 GHz."""
+    return 148 * 128 * 2 * 2.032e9 / 1e12
+
+
+def sweep_cpu_baseline(params, sample=6):
+    """The oracle's Alg. 4 (oracle/krylov.py, FP64) on `sample` instances of the sweep spread over n,
+    scaled to the whole sweep by sum n^3."""
+    import numpy as np
+
+    import lindblad_inputs as gi
+    from oracle import krylov as K
+
+    order = np.argsort([p["n"] for p in params])
+    picks = [int(order[int(i)]) for i in np.linspace(0, len(order) - 1, sample)]
+    t_sum, w_sum = 0.0, 0.0
+    for k in picks:
+        p = params[k]
+        H, Ls = gi.kerr_cat(p["n"], K=p["K"], eps2=p["eps2"], kappa2=p["kappa2"], kappa1=p["kappa1"])
+        t0 = time.perf_counter()
+        K.steady_state_phi_arnoldi(K.System(H, Ls), tol=1e-10, m=30, N=60)
+        t_sum += time.perf_counter() - t0
+        w_sum += p["n"] ** 3
+    total = t_sum * sum(p["n"] ** 3 for p in params) / w_sum
+    return {"value": len(params) / total, "unit": "steady-states/s", "cores": len(os.sched_getaffinity(0)),
+            "kind": "oracle", "sample": (f"oracle Alg. 4 (m=30) on {sample} sweep instances "
+                                         f"(n={sorted(params[k]['n'] for k in picks)}), {t_sum:.1f} s, scaled "
+                                         f"by sum n^3 to the 1024-instance sweep ({total:.0f} s)")}
+
+
+def run_sweep(args, world, device):
+    import numpy as np
+    import torch
+
+    import lindblad_inputs as gi
+    import paper_2608_30860_b300 as B
+
+    torch.cuda.set_device(device)
+    params = gi.kerr_cat_sweep(SWEEP["count"], seed=SWEEP["seed"])
+    systems = [gi.kerr_cat(p["n"], K=p["K"], eps2=p["eps2"], kappa2=p["kappa2"], kappa1=p["kappa1"])
+               for p in params]
+    ns = [p["n"] for p in params]
+    d = 2
+    Hh = torch.from_numpy(np.concatenate([H.reshape(-1) for H, _ in systems])).pin_memory()
+    Lh = torch.from_numpy(np.concatenate([np.stack(L).reshape(-1) for _, L in systems])).pin_memory()
+    Hd, Ld = Hh.to(device), Lh.to(device)
+    rho = torch.empty_like(Hd)
+    ws = torch.empty(B.lindblad_batched_workspace_bytes(ns, d), dtype=torch.uint8, device=device)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        B.steady_state_batched(ns, d, Hd, Ld, rho=rho, workspace=ws)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_launch0 = B.lb_launch_count()
+    applies = 0
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        torch.cuda.profiler.start()
+        e0.record(stream)
+        for _ in range(args.steps):
+            _, infos, st = B.steady_state_batched(ns, d, Hd, Ld, rho=rho, workspace=ws)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = e0.elapsed_time(e1)
+    gpu_launches = B.lb_launch_count() - n_launch0
+    worst = max(i["residual_max"] for i in infos)
+    applies = [i["phi_applies"] for i in infos]
+    anchors = [i["refine_steps"] for i in infos]
+    flops32 = sum(a * (2 * d + 1) * n ** 3 * 8.0 for a, n in zip(applies, ns))
+    # end to end: pinned host H, L in, rho out, inside the timed region
+    rho_h = torch.empty_like(Hh).pin_memory()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(args.steps):
+        Hd.copy_(Hh, non_blocking=True)
+        Ld.copy_(Lh, non_blocking=True)
+        B.steady_state_batched(ns, d, Hd, Ld, rho=rho, workspace=ws)
+        rho_h.copy_(rho, non_blocking=True)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = f0.elapsed_time(f1)
+    return dict(ms=ms, e2e_ms=e2e_ms, clocks=clk.summary(), gpu_launches=gpu_launches, status=st,
+                worst=worst, applies=applies, anchors=anchors, flops32=flops32, params=params,
+                h2d=int(Hh.numel() + Lh.numel()) * 16, d2h=int(rho_h.numel()) * 16, ws_bytes=ws.numel())
+
+
+def sweep_line(args, r, world):
+    count = SWEEP["count"]
+    value = count * args.steps * world / (r["ms"] / 1000.0)
+    per_sweep_s = r["ms"] / 1000.0 / args.steps
+    achieved = r["flops32"] / per_sweep_s / 1e12
+    peak = fp32_alu_peak_tflops()
+    line = {
+        "metric": "steady states/s of the batched Kerr-cat sweep (1024 instances, n in 16..160), resid<=1e-10",
+        "value": value, "unit": "steady-states/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": r["ms"] / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64+f64", "data": "synthetic",
+        "config": dict(SWEEP, parallelism="replicas" if world > 1 else "none",
+                       l2=f"one step = the whole sweep ({r['ws_bytes'] / 1e9:.1f} GB of per-instance state) > L2; "
+                          "no flush"),
+        "roofline": {"bound": "alu", "kernel": "k_batched_solve (persistent, one CTA per instance)",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": None,
+                     "peak_source": "FP32 CUDA-core peak from 148 SMs x 128 FMA/clk x 2 x 2.032 GHz",
+                     "flops_per_step": r["flops32"],
+                     "note": "algorithmic complex64 flops of the Phi applications (jump term + triangular solve); "
+                             "the FP64 anchors and the set-up are not counted"},
+        "e2e": {"value": count * args.steps / (r["e2e_ms"] / 1000.0), "unit": "steady-states/s",
+                "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
+        "gpu_launches": r["gpu_launches"],
+        "clocks": r["clocks"],
+        "status": r["status"], "worst_residual_max": r["worst"],
+        "phi_applies_mean": sum(r["applies"]) / count, "fp64_anchors_mean": sum(r["anchors"]) / count,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = sweep_cpu_baseline(r["params"])
+    return line
+
+
 def run_ours(args, rank, world, device):
     import numpy as np
     import torch
@@ -216,6 +344,8 @@ def main():
     ap.add_argument("--solve", action="store_true", help="also time one mixed steady-state solve")
     ap.add_argument("--fp64", action="store_true", help="also time one all-FP64 Phi application")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="tfim12", choices=["tfim12", "sweep"],
+                    help="tfim12: Phi applications at n=4096 (default); sweep: the batched Kerr-cat sweep")
     ap.add_argument("--sites", type=int, default=12,
                     help="chain length (12: the n=4096 workload; smaller values give the small cases "
                          "used for profiler captures)")
@@ -245,6 +375,18 @@ def main():
     if world > 1:
         torch.distributed.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     device = torch.device("cuda", local)
+    if args.workload == "sweep":
+        r = run_sweep(args, world, device)
+        ms = r["ms"]
+        if world > 1:
+            t = torch.tensor([ms, r["e2e_ms"]], dtype=torch.float64, device=device)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            r["ms"], r["e2e_ms"] = float(t[0]), float(t[1])
+        if rank == 0:
+            print(json.dumps(sweep_line(args, r, world)))
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
     r = run_ours(args, rank, world, device)
     ms = r["ms"]
     if world > 1:
