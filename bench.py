@@ -247,6 +247,39 @@ def sweep_line(args, r, world):
     return line
 
 
+def measure_peaks(device):
+    """Library-GEMM throughput of the units the batched and FP64 paths use (cuBLAS through torch,
+    best of 5 after warm-up, CUDA events): FP64, FP32 (TF32 off), TF32, complex64, complex128."""
+    import torch
+
+    torch.cuda.set_device(device)
+    out = {}
+    cases = [("fp64", torch.float64, 4096, False, 2), ("fp32", torch.float32, 8192, False, 2),
+             ("tf32", torch.float32, 8192, True, 2), ("c64", torch.complex64, 4096, False, 8),
+             ("c128", torch.complex128, 2048, False, 8)]
+    for name, dt, n, tf32, fl in cases:
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        a = torch.randn(n, n, dtype=dt, device=device)
+        b = torch.randn(n, n, dtype=dt, device=device)
+        for _ in range(2):
+            a @ b
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            a @ b
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        out[name + "_tflops"] = fl * n ** 3 / (best / 1000.0) / 1e12
+        del a, b
+    torch.backends.cuda.matmul.allow_tf32 = False
+    out["fp32_alu_peak_tflops_derived"] = fp32_alu_peak_tflops()
+    return out
+
+
 def run_ours(args, rank, world, device):
     import numpy as np
     import torch
@@ -344,6 +377,8 @@ def main():
     ap.add_argument("--solve", action="store_true", help="also time one mixed steady-state solve")
     ap.add_argument("--fp64", action="store_true", help="also time one all-FP64 Phi application")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--peaks", action="store_true",
+                    help="only measure library GEMM peaks (FP64, FP32, TF32, complex64/128) and print them")
     ap.add_argument("--workload", default="tfim12", choices=["tfim12", "sweep"],
                     help="tfim12: Phi applications at n=4096 (default); sweep: the batched Kerr-cat sweep")
     ap.add_argument("--sites", type=int, default=12,
@@ -375,6 +410,12 @@ def main():
     if world > 1:
         torch.distributed.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     device = torch.device("cuda", local)
+    if args.peaks:
+        if rank == 0:
+            with ClockSampler(torch.cuda.current_device()) as clk:
+                pk = measure_peaks(device)
+            print(json.dumps({"peaks": pk, "clocks": clk.summary()}))
+        return
     if args.workload == "sweep":
         r = run_sweep(args, world, device)
         ms = r["ms"]

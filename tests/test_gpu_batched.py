@@ -166,3 +166,21 @@ def test_batched_full_sweep_sampled_oracle_parity(full_sweep):
         err = np.linalg.norm(ge - re_) / np.linalg.norm(re_)
         print(f"instance {k} n={H.shape[0]} even-sector err {err:.2e} oracle residual {res:.1e}")
         assert err < 1e-8
+
+
+def test_batched_matches_single_instance_fp64_path(B, full_sweep):
+    """Sampled sweep instances against the single-instance FP64 steady_state (Alg. 4 on the same
+    Lindbladian through lindblad_setup), compared on the parity-even part."""
+    params, systems, rhos, infos, st = full_sweep
+    picks = [k for k, p in enumerate(params) if p["kappa1"] > 0.05][:3]
+    picks += [int(np.argmax([p["n"] if p["kappa1"] > 0.05 else 0 for p in params]))]
+    for k in picks:
+        H, Ls = systems[k]
+        h = B.lindblad_setup(_cuda(H), _cuda(np.stack(Ls)))
+        ref, info, st1 = B.steady_state(h, B.default_opts(tol=TOL, krylov_m=30, max_restarts=200))
+        B.lindblad_destroy(h)
+        assert st1 == 0, info
+        ge, re_ = _parity_even(rhos[k].cpu().numpy()), _parity_even(ref.cpu().numpy())
+        err = np.linalg.norm(ge - re_) / np.linalg.norm(re_)
+        print(f"instance {k} n={H.shape[0]} vs single-instance FP64: even-sector err {err:.2e}")
+        assert err < 1e-8
