@@ -162,7 +162,7 @@ def run_sweep(args, world, device):
     import paper_2608_30860_b300 as B
 
     torch.cuda.set_device(device)
-    params = gi.kerr_cat_sweep(SWEEP["count"], seed=SWEEP["seed"])
+    params = gi.kerr_cat_sweep(args.sweep_count, seed=SWEEP["seed"], nmin=args.sweep_n[0], nmax=args.sweep_n[1])
     systems = [gi.kerr_cat(p["n"], K=p["K"], eps2=p["eps2"], kappa2=p["kappa2"], kappa1=p["kappa1"])
                for p in params]
     ns = [p["n"] for p in params]
@@ -215,7 +215,7 @@ def run_sweep(args, world, device):
 
 
 def sweep_line(args, r, world):
-    count = SWEEP["count"]
+    count = args.sweep_count
     value = count * args.steps * world / (r["ms"] / 1000.0)
     per_sweep_s = r["ms"] / 1000.0 / args.steps
     achieved = r["flops32"] / per_sweep_s / 1e12
@@ -225,7 +225,7 @@ def sweep_line(args, r, world):
         "value": value, "unit": "steady-states/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": r["ms"] / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "c64+f64", "data": "synthetic",
-        "config": dict(SWEEP, parallelism="replicas" if world > 1 else "none",
+        "config": dict(SWEEP, count=count, n_range=list(args.sweep_n), parallelism="replicas" if world > 1 else "none",
                        l2=f"one step = the whole sweep ({r['ws_bytes'] / 1e9:.1f} GB of per-instance state) > L2; "
                           "no flush"),
         "roofline": {"bound": "alu", "kernel": "k_batched_solve (persistent, one CTA per instance)",
@@ -381,6 +381,9 @@ def main():
                     help="only measure library GEMM peaks (FP64, FP32, TF32, complex64/128) and print them")
     ap.add_argument("--workload", default="tfim12", choices=["tfim12", "sweep"],
                     help="tfim12: Phi applications at n=4096 (default); sweep: the batched Kerr-cat sweep")
+    ap.add_argument("--sweep-count", type=int, default=SWEEP["count"],
+                    help="instances of the sweep (1024: the benchmark; small values give profiler cases)")
+    ap.add_argument("--sweep-n", type=int, nargs=2, default=SWEEP["n_range"], metavar=("NMIN", "NMAX"))
     ap.add_argument("--sites", type=int, default=12,
                     help="chain length (12: the n=4096 workload; smaller values give the small cases "
                          "used for profiler captures)")
