@@ -7,8 +7,8 @@
 //         C_IJ -= sum_{K>I} T_IK X_KJ + sum_{L>J} X_IL T_JL^dag,
 //       one tcgen05 CTA per block (tc_gemm.cu, wavefront mode, BF16 hi/lo operands -- BF16 keeps
 //       FP32's exponent range, so the unknown magnitude of X needs no scale);
-//   (2) the leaf solve of each block in FP32 on the CUDA cores: a left-looking sweep over the
-//       block's 255 anti-diagonals (4 threads per entry).  The leaf writes X_IJ back (complex128)
+//   (2) the leaf solve of each block in FP32 on the CUDA cores, itself blocked: 32 x 32
+//       sub-blocks by anti-diagonals, each a small GEMM update plus a 32 x 32 anti-diagonal sweep.  The leaf writes X_IJ back (complex128)
 //       and refreshes the BF16 planes of X and X^T that the later updates read.
 #include <cuda_bf16.h>
 
@@ -29,11 +29,9 @@ struct SylvMixed {
 namespace {
 
 constexpr int LB = 128;   // wavefront block
-constexpr int LEAF_THREADS = 512;   // 4 threads per entry of an anti-diagonal (<= 128 entries)
-// shared-memory row pitch in complex floats.  A warp holds 8 anti-diagonal entries (slot s,
-// a = a0 + s, b = S - a) x 4 threads t; its loads X[a+1+t][b] and X[a][b+1+t] sit at word offsets
-// (pitch-1) s + pitch t and (pitch-1) s + t.  With pitch = 5 (mod 32) both sets cover the 32
-// eight-byte bank pairs exactly once.
+constexpr int LEAF_THREADS = 512;
+// shared-memory row pitch of the block in complex floats: a column walk of 16 rows (the leaf's
+// per-entry split) lands on 16 distinct bank pairs (10 r mod 32)
 constexpr int PITCH = LB + 5;
 
 struct f2 {
@@ -43,19 +41,25 @@ __device__ __forceinline__ f2 fmk(float a, float b) { return f2{a, b}; }
 
 __device__ __forceinline__ f2 f2ld(const float2* p) { const float2 v = __ldg(p); return fmk(v.x, v.y); }
 
-// Leaf of one 128 x 128 block (I, J) of the wavefront: A X + X B^dag = C with A = T_II - sI,
-// B = T_JJ - sI (upper triangular), C already updated by the tensor-core step.  Left-looking
-// anti-diagonal sweep over the whole block: the entries (a, b) with a + b = S are independent and
-//   X_ab = (C_ab - sum_{r>a} A_ar X_rb - sum_{r>b} X_ar conj(B_br)) / (A_aa + conj(B_bb)),
-// each dot product of the same length 254 - S, split over 4 threads and reduced by shuffles.
-// A is kept in shared memory as a packed upper triangle; B rows are read through L1/L2.
+constexpr int SB = 32;        // sub-block of the sweep inside a leaf
+constexpr int SP = SB + 1;    // pitch of the staged T tiles
+
+// Leaf of one 128 x 128 block (I, J) of the wavefront: A Y + Y B^dag = C with A = T_II - sI,
+// B = T_JJ - sI (upper triangular), C already updated by the tensor-core step and held in shared
+// memory.  The block is swept in 32 x 32 sub-blocks (p, q) by decreasing p + q: a sub-block first
+// subtracts its coupling to the solved ones, sum_{k>p} A_pk Y_kq + sum_{k>q} Y_pk B_qk^dag (A and B
+// tiles staged from the FP32 copy of T, Y read in place; 2 outputs per thread), then solves its own
+// 32 x 32 system by anti-diagonals,
+//   Y_ab = (C_ab - sum_{r>a} A_ar Y_rb - sum_{r>b} Y_ar conj(B_br)) / (A_aa + conj(B_bb)),
+// with 16 threads per entry reduced by shuffles, everything in shared memory.
 __global__ void __launch_bounds__(LEAF_THREADS, 1)
 k_sylv_leaf128(const float2* __restrict__ Tf, const float2* __restrict__ Ttf, int ldf, cplx* __restrict__ X, int n,
                float sh, int wave, int nb, __nv_bfloat16* __restrict__ Xp, __nv_bfloat16* __restrict__ XTp,
                int np) {
     extern __shared__ __align__(16) unsigned char smraw[];
     f2(*Xs)[PITCH] = reinterpret_cast<f2(*)[PITCH]>(smraw);                       // 128 x PITCH
-    f2* Ap = reinterpret_cast<f2*>(smraw + sizeof(f2) * LB * PITCH);              // packed upper triangle
+    f2* ta = reinterpret_cast<f2*>(smraw + sizeof(f2) * LB * PITCH);              // SB x SP
+    f2* tb = ta + SB * SP;                                                         // SB x SP
     const int t = blockIdx.x + max(0, wave - (nb - 1));
     const int I = nb - 1 - t, J = nb - 1 - (wave - t);
     const int r0 = I * LB, c0 = J * LB;
@@ -65,74 +69,107 @@ k_sylv_leaf128(const float2* __restrict__ Tf, const float2* __restrict__ Ttf, in
 
     for (int e = tid; e < LB * LB; e += LEAF_THREADS) {
         const int p = e / LB, q = e % LB;
-        cplx v = (p < br && q < bc) ? X[(long long)(r0 + p) * n + c0 + q] : cmake(0, 0);
+        const cplx v = (p < br && q < bc) ? X[(long long)(r0 + p) * n + c0 + q] : cmake(0, 0);
         Xs[p][q] = fmk((float)v.x, (float)v.y);
-        if (q >= p) {
-            f2 a = (p < br && q < br) ? f2ld(Tf + (long long)(r0 + p) * ldf + r0 + q) : fmk(0.f, 0.f);
-            if (q == p) a.x -= sh;
-            Ap[p * LB - (p * (p - 1)) / 2 + (q - p)] = a;
-        }
     }
     __syncthreads();
 
-    const int slot = tid >> 2, t4 = tid & 3;
-    for (int S = (br - 1) + (bc - 1); S >= 0; --S) {
-        const int a = max(0, S - (bc - 1)) + slot;
-        const int b = S - a;
-        const bool valid = a < br && b >= 0 && a <= S;
-        f2 acc = fmk(0.f, 0.f);
-        if (valid) {
-            // four independent partial sums so that four loads are in flight
-            f2 p[4] = {fmk(0.f, 0.f), fmk(0.f, 0.f), fmk(0.f, 0.f), fmk(0.f, 0.f)};
-            const int arow = a * LB - (a * (a - 1)) / 2 - a;      // Ap index of A[a][r] = arow + r
-            int r = a + 1 + t4;
-            for (; r + 12 < br; r += 16) {
+    const int tx = tid & 31, ty = tid >> 5;          // 16 x 32: rows ty and ty + 16 of a sub-block
+    const int slot = tid >> 4, t16 = tid & 15;       // leaf: 32 entries x 16 threads
+    const int nsr = (br + SB - 1) / SB, nsc = (bc + SB - 1) / SB;
+    for (int s = (nsr - 1) + (nsc - 1); s >= 0; --s) {
+        for (int p = max(0, s - (nsc - 1)); p <= min(s, nsr - 1); ++p) {
+            const int q = s - p;
+            const int pr = p * SB, qc = q * SB;
+            f2 acc0 = fmk(0.f, 0.f), acc1 = fmk(0.f, 0.f);
+            // sum_{k>p} A_pk Y_kq
+            for (int k0 = pr + SB; k0 < br; k0 += SB) {
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const f2 m = Ap[arow + r + 4 * u], x = Xs[r + 4 * u][b];
-                    p[u].x += m.x * x.x - m.y * x.y;
-                    p[u].y += m.x * x.y + m.y * x.x;
+                for (int i = 0; i < 2; ++i) {
+                    const int rr = ty + 16 * i;
+                    ta[rr * SP + tx] = (pr + rr < br && k0 + tx < br)
+                                           ? f2ld(Tf + (long long)(r0 + pr + rr) * ldf + r0 + k0 + tx) : fmk(0.f, 0.f);
                 }
-            }
-            for (; r < br; r += 4) {
-                const f2 m = Ap[arow + r], x = Xs[r][b];
-                p[0].x += m.x * x.x - m.y * x.y;
-                p[0].y += m.x * x.y + m.y * x.x;
-            }
-            const float2* brow = Tf + (long long)(c0 + b) * ldf + c0;
-            r = b + 1 + t4;
-            for (; r + 12 < bc; r += 16) {
-                f2 m[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) m[u] = f2ld(brow + r + 4 * u);
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const f2 x = Xs[a][r + 4 * u];
-                    p[u].x += x.x * m[u].x + x.y * m[u].y;
-                    p[u].y += x.y * m[u].x - x.x * m[u].y;
+                __syncthreads();
+#pragma unroll 8
+                for (int k = 0; k < SB; ++k) {
+                    const f2 y = Xs[k0 + k][qc + tx];
+                    const f2 m0 = ta[ty * SP + k], m1 = ta[(ty + 16) * SP + k];
+                    acc0.x += m0.x * y.x - m0.y * y.y;
+                    acc0.y += m0.x * y.y + m0.y * y.x;
+                    acc1.x += m1.x * y.x - m1.y * y.y;
+                    acc1.y += m1.x * y.y + m1.y * y.x;
                 }
+                __syncthreads();
             }
-            for (; r < bc; r += 4) {
-                const f2 x = Xs[a][r], m = f2ld(brow + r);
-                p[1].x += x.x * m.x + x.y * m.y;
-                p[1].y += x.y * m.x - x.x * m.y;
+            // sum_{k>q} Y_pk B_qk^dag  (tb[k][j] = conj(B[qc + j][k0 + k]): coalesced load, transposed store)
+            for (int k0 = qc + SB; k0 < bc; k0 += SB) {
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const int rr = ty + 16 * i;
+                    f2 v = (qc + rr < bc && k0 + tx < bc) ? f2ld(Tf + (long long)(c0 + qc + rr) * ldf + c0 + k0 + tx)
+                                                          : fmk(0.f, 0.f);
+                    v.y = -v.y;
+                    tb[tx * SP + rr] = v;
+                }
+                __syncthreads();
+#pragma unroll 8
+                for (int k = 0; k < SB; ++k) {
+                    const f2 m = tb[k * SP + tx];
+                    const f2 y0 = Xs[pr + ty][k0 + k], y1 = Xs[pr + ty + 16][k0 + k];
+                    acc0.x += y0.x * m.x - y0.y * m.y;
+                    acc0.y += y0.x * m.y + y0.y * m.x;
+                    acc1.x += y1.x * m.x - y1.y * m.y;
+                    acc1.y += y1.x * m.y + y1.y * m.x;
+                }
+                __syncthreads();
             }
-            acc = fmk((p[0].x + p[1].x) + (p[2].x + p[3].x), (p[0].y + p[1].y) + (p[2].y + p[3].y));
+            // right-hand side of the sub-block and its diagonal tiles A_pp, B_qq
+            Xs[pr + ty][qc + tx].x -= acc0.x;
+            Xs[pr + ty][qc + tx].y -= acc0.y;
+            Xs[pr + ty + 16][qc + tx].x -= acc1.x;
+            Xs[pr + ty + 16][qc + tx].y -= acc1.y;
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int rr = ty + 16 * i;
+                ta[rr * SP + tx] = (pr + rr < br && pr + tx < br)
+                                       ? f2ld(Tf + (long long)(r0 + pr + rr) * ldf + r0 + pr + tx) : fmk(0.f, 0.f);
+                tb[rr * SP + tx] = (qc + rr < bc && qc + tx < bc)
+                                       ? f2ld(Tf + (long long)(c0 + qc + rr) * ldf + c0 + qc + tx) : fmk(0.f, 0.f);
+            }
+            __syncthreads();
+            for (int d = 2 * SB - 2; d >= 0; --d) {
+                const int alo = max(0, d - (SB - 1)), cnt = min(d, SB - 1) - alo + 1;
+                const bool valid = slot < cnt;
+                const int a = alo + slot, b = d - a;
+                f2 acc = fmk(0.f, 0.f);
+                if (valid) {
+                    for (int r = a + 1 + t16; r < SB; r += 16) {
+                        const f2 m = ta[a * SP + r], y = Xs[pr + r][qc + b];
+                        acc.x += m.x * y.x - m.y * y.y;
+                        acc.y += m.x * y.y + m.y * y.x;
+                    }
+                    for (int r = b + 1 + t16; r < SB; r += 16) {
+                        const f2 y = Xs[pr + a][qc + r], m = tb[b * SP + r];
+                        acc.x += y.x * m.x + y.y * m.y;
+                        acc.y += y.y * m.x - y.x * m.y;
+                    }
+                }
+#pragma unroll
+                for (int o = 1; o < 16; o <<= 1) {
+                    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+                    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+                }
+                if (valid && t16 == 0 && pr + a < br && qc + b < bc) {
+                    const f2 da = ta[a * SP + a], db = tb[b * SP + b];
+                    const float dr = (da.x - sh) + (db.x - sh), di = da.y - db.y;   // A_aa + conj(B_bb)
+                    const float inv = 1.0f / (dr * dr + di * di);
+                    const f2 v = fmk(Xs[pr + a][qc + b].x - acc.x, Xs[pr + a][qc + b].y - acc.y);
+                    Xs[pr + a][qc + b] = fmk((v.x * dr + v.y * di) * inv, (v.y * dr - v.x * di) * inv);
+                }
+                __syncthreads();
+            }
         }
-        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
-        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
-        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 2);
-        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 2);
-        if (valid && t4 == 0) {
-            const f2 da = Ap[a * LB - (a * (a - 1)) / 2];
-            f2 db = f2ld(Tf + (long long)(c0 + b) * ldf + c0 + b);
-            db.x -= sh;
-            const float dr = da.x + db.x, di = da.y - db.y;   // A_aa + conj(B_bb)
-            const float inv = 1.0f / (dr * dr + di * di);
-            const f2 v = fmk(Xs[a][b].x - acc.x, Xs[a][b].y - acc.y);
-            Xs[a][b] = fmk((v.x * dr + v.y * di) * inv, (v.y * dr - v.x * di) * inv);
-        }
-        __syncthreads();
     }
     // write back: complex128 block and the BF16 hi/lo planes of X (rows), lanes along q ...
     const long long ps = (long long)np * np;
@@ -172,7 +209,7 @@ __global__ void k_t_to_f32(const cplx* __restrict__ T, int n, float2* __restrict
     }
 }
 
-constexpr size_t LEAF_SMEM = sizeof(f2) * LB * PITCH + sizeof(f2) * (LB * (LB + 1) / 2);
+constexpr size_t LEAF_SMEM = sizeof(f2) * LB * PITCH + 2 * sizeof(f2) * SB * SP;
 
 inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
