@@ -12,12 +12,15 @@
 //       and refreshes the BF16 planes of X and X^T that the later updates read.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "lb_internal.cuh"
 #include "tc_gemm.cuh"
 #include "vecops.cuh"
 
 struct SylvMixed {
     int np = 0, nb = 0;
+    int sms = 148;                  // multiprocessors of the device (split-K of the wave updates)
     __nv_bfloat16* Tp = nullptr;    // 4 x np x np, rows of T (unshifted)
     __nv_bfloat16* Xp = nullptr;    // 4 x np x np, rows of X
     __nv_bfloat16* XTp = nullptr;   // 4 x np x np, rows of X^T
@@ -41,25 +44,28 @@ __device__ __forceinline__ f2 fmk(float a, float b) { return f2{a, b}; }
 
 __device__ __forceinline__ f2 f2ld(const float2* p) { const float2 v = __ldg(p); return fmk(v.x, v.y); }
 
+// barrier of one 128-thread group (named barriers 1..4; 0 is __syncthreads)
+__device__ __forceinline__ void group_sync(int g) { asm volatile("bar.sync %0, 128;" ::"r"(g + 1) : "memory"); }
+
 constexpr int SB = 32;        // sub-block of the sweep inside a leaf
 constexpr int SP = SB + 1;    // pitch of the staged T tiles
 
 // Leaf of one 128 x 128 block (I, J) of the wavefront: A Y + Y B^dag = C with A = T_II - sI,
 // B = T_JJ - sI (upper triangular), C already updated by the tensor-core step and held in shared
-// memory.  The block is swept in 32 x 32 sub-blocks (p, q) by decreasing p + q: a sub-block first
-// subtracts its coupling to the solved ones, sum_{k>p} A_pk Y_kq + sum_{k>q} Y_pk B_qk^dag (A and B
-// tiles staged from the FP32 copy of T, Y read in place; 2 outputs per thread), then solves its own
-// 32 x 32 system by anti-diagonals,
+// memory.  The block is swept in 32 x 32 sub-blocks (p, q) by decreasing p + q, the sub-blocks of
+// one p + q in parallel (a 128-thread group each): a sub-block first subtracts its coupling to the
+// solved ones, sum_{k>p} A_pk Y_kq + sum_{k>q} Y_pk B_qk^dag (A and B tiles staged from the FP32
+// copy of T, Y read in place; 8 outputs per thread), then solves its own 32 x 32 system by
+// anti-diagonals,
 //   Y_ab = (C_ab - sum_{r>a} A_ar Y_rb - sum_{r>b} Y_ar conj(B_br)) / (A_aa + conj(B_bb)),
-// with 16 threads per entry reduced by shuffles, everything in shared memory.
+// with 4 threads per entry reduced by shuffles, everything in shared memory.
 __global__ void __launch_bounds__(LEAF_THREADS, 1)
 k_sylv_leaf128(const float2* __restrict__ Tf, const float2* __restrict__ Ttf, int ldf, cplx* __restrict__ X, int n,
                float sh, int wave, int nb, __nv_bfloat16* __restrict__ Xp, __nv_bfloat16* __restrict__ XTp,
                int np) {
     extern __shared__ __align__(16) unsigned char smraw[];
     f2(*Xs)[PITCH] = reinterpret_cast<f2(*)[PITCH]>(smraw);                       // 128 x PITCH
-    f2* ta = reinterpret_cast<f2*>(smraw + sizeof(f2) * LB * PITCH);              // SB x SP
-    f2* tb = ta + SB * SP;                                                         // SB x SP
+    f2* ta = reinterpret_cast<f2*>(smraw + sizeof(f2) * LB * PITCH);              // 4 groups x 2 x SB x SP
     const int t = blockIdx.x + max(0, wave - (nb - 1));
     const int I = nb - 1 - t, J = nb - 1 - (wave - t);
     const int r0 = I * LB, c0 = J * LB;
@@ -74,102 +80,111 @@ k_sylv_leaf128(const float2* __restrict__ Tf, const float2* __restrict__ Ttf, in
     }
     __syncthreads();
 
-    const int tx = tid & 31, ty = tid >> 5;          // 16 x 32: rows ty and ty + 16 of a sub-block
-    const int slot = tid >> 4, t16 = tid & 15;       // leaf: 32 entries x 16 threads
+    // four groups of 128 threads: the sub-blocks of one sub-anti-diagonal (at most 4) run side by
+    // side, each group synchronising on its own named barrier
+    const int g = tid >> 7, lt = tid & 127;
+    const int tx = lt & 31, ty = lt >> 5;            // rows ty + 4 i (i < 8) of the group's sub-block
+    const int slot = lt >> 2, t4 = lt & 3;           // leaf: 32 entries x 4 threads
+    f2* ga = ta + g * 2 * SB * SP;                   // the group's two staging tiles
+    f2* gb = ga + SB * SP;
     const int nsr = (br + SB - 1) / SB, nsc = (bc + SB - 1) / SB;
     for (int s = (nsr - 1) + (nsc - 1); s >= 0; --s) {
-        for (int p = max(0, s - (nsc - 1)); p <= min(s, nsr - 1); ++p) {
+        const int p = max(0, s - (nsc - 1)) + g;
+        if (p <= min(s, nsr - 1)) {
             const int q = s - p;
             const int pr = p * SB, qc = q * SB;
-            f2 acc0 = fmk(0.f, 0.f), acc1 = fmk(0.f, 0.f);
+            f2 acc[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) acc[i] = fmk(0.f, 0.f);
             // sum_{k>p} A_pk Y_kq
             for (int k0 = pr + SB; k0 < br; k0 += SB) {
 #pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    const int rr = ty + 16 * i;
-                    ta[rr * SP + tx] = (pr + rr < br && k0 + tx < br)
+                for (int i = 0; i < 8; ++i) {
+                    const int rr = ty + 4 * i;
+                    ga[rr * SP + tx] = (pr + rr < br && k0 + tx < br)
                                            ? f2ld(Tf + (long long)(r0 + pr + rr) * ldf + r0 + k0 + tx) : fmk(0.f, 0.f);
                 }
-                __syncthreads();
-#pragma unroll 8
+                group_sync(g);
+#pragma unroll 4
                 for (int k = 0; k < SB; ++k) {
                     const f2 y = Xs[k0 + k][qc + tx];
-                    const f2 m0 = ta[ty * SP + k], m1 = ta[(ty + 16) * SP + k];
-                    acc0.x += m0.x * y.x - m0.y * y.y;
-                    acc0.y += m0.x * y.y + m0.y * y.x;
-                    acc1.x += m1.x * y.x - m1.y * y.y;
-                    acc1.y += m1.x * y.y + m1.y * y.x;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const f2 m = ga[(ty + 4 * i) * SP + k];
+                        acc[i].x += m.x * y.x - m.y * y.y;
+                        acc[i].y += m.x * y.y + m.y * y.x;
+                    }
                 }
-                __syncthreads();
+                group_sync(g);
             }
-            // sum_{k>q} Y_pk B_qk^dag  (tb[k][j] = conj(B[qc + j][k0 + k]): coalesced load, transposed store)
+            // sum_{k>q} Y_pk B_qk^dag  (gb[k][j] = conj(B[qc + j][k0 + k]): coalesced load, transposed store)
             for (int k0 = qc + SB; k0 < bc; k0 += SB) {
 #pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    const int rr = ty + 16 * i;
+                for (int i = 0; i < 8; ++i) {
+                    const int rr = ty + 4 * i;
                     f2 v = (qc + rr < bc && k0 + tx < bc) ? f2ld(Tf + (long long)(c0 + qc + rr) * ldf + c0 + k0 + tx)
                                                           : fmk(0.f, 0.f);
                     v.y = -v.y;
-                    tb[tx * SP + rr] = v;
+                    gb[tx * SP + rr] = v;
                 }
-                __syncthreads();
-#pragma unroll 8
+                group_sync(g);
+#pragma unroll 4
                 for (int k = 0; k < SB; ++k) {
-                    const f2 m = tb[k * SP + tx];
-                    const f2 y0 = Xs[pr + ty][k0 + k], y1 = Xs[pr + ty + 16][k0 + k];
-                    acc0.x += y0.x * m.x - y0.y * m.y;
-                    acc0.y += y0.x * m.y + y0.y * m.x;
-                    acc1.x += y1.x * m.x - y1.y * m.y;
-                    acc1.y += y1.x * m.y + y1.y * m.x;
+                    const f2 m = gb[k * SP + tx];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const f2 y = Xs[pr + ty + 4 * i][k0 + k];
+                        acc[i].x += y.x * m.x - y.y * m.y;
+                        acc[i].y += y.x * m.y + y.y * m.x;
+                    }
                 }
-                __syncthreads();
+                group_sync(g);
             }
             // right-hand side of the sub-block and its diagonal tiles A_pp, B_qq
-            Xs[pr + ty][qc + tx].x -= acc0.x;
-            Xs[pr + ty][qc + tx].y -= acc0.y;
-            Xs[pr + ty + 16][qc + tx].x -= acc1.x;
-            Xs[pr + ty + 16][qc + tx].y -= acc1.y;
 #pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                const int rr = ty + 16 * i;
-                ta[rr * SP + tx] = (pr + rr < br && pr + tx < br)
+            for (int i = 0; i < 8; ++i) {
+                const int rr = ty + 4 * i;
+                Xs[pr + rr][qc + tx].x -= acc[i].x;
+                Xs[pr + rr][qc + tx].y -= acc[i].y;
+                ga[rr * SP + tx] = (pr + rr < br && pr + tx < br)
                                        ? f2ld(Tf + (long long)(r0 + pr + rr) * ldf + r0 + pr + tx) : fmk(0.f, 0.f);
-                tb[rr * SP + tx] = (qc + rr < bc && qc + tx < bc)
+                gb[rr * SP + tx] = (qc + rr < bc && qc + tx < bc)
                                        ? f2ld(Tf + (long long)(c0 + qc + rr) * ldf + c0 + qc + tx) : fmk(0.f, 0.f);
             }
-            __syncthreads();
+            group_sync(g);
             for (int d = 2 * SB - 2; d >= 0; --d) {
                 const int alo = max(0, d - (SB - 1)), cnt = min(d, SB - 1) - alo + 1;
                 const bool valid = slot < cnt;
                 const int a = alo + slot, b = d - a;
-                f2 acc = fmk(0.f, 0.f);
+                f2 acc0 = fmk(0.f, 0.f), acc1 = fmk(0.f, 0.f);
                 if (valid) {
-                    for (int r = a + 1 + t16; r < SB; r += 16) {
-                        const f2 m = ta[a * SP + r], y = Xs[pr + r][qc + b];
-                        acc.x += m.x * y.x - m.y * y.y;
-                        acc.y += m.x * y.y + m.y * y.x;
+                    for (int r = a + 1 + t4; r < SB; r += 4) {
+                        const f2 m = ga[a * SP + r], y = Xs[pr + r][qc + b];
+                        acc0.x += m.x * y.x - m.y * y.y;
+                        acc0.y += m.x * y.y + m.y * y.x;
                     }
-                    for (int r = b + 1 + t16; r < SB; r += 16) {
-                        const f2 y = Xs[pr + a][qc + r], m = tb[b * SP + r];
-                        acc.x += y.x * m.x + y.y * m.y;
-                        acc.y += y.y * m.x - y.x * m.y;
+                    for (int r = b + 1 + t4; r < SB; r += 4) {
+                        const f2 y = Xs[pr + a][qc + r], m = gb[b * SP + r];
+                        acc1.x += y.x * m.x + y.y * m.y;
+                        acc1.y += y.y * m.x - y.x * m.y;
                     }
                 }
-#pragma unroll
-                for (int o = 1; o < 16; o <<= 1) {
-                    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-                    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-                }
-                if (valid && t16 == 0 && pr + a < br && qc + b < bc) {
-                    const f2 da = ta[a * SP + a], db = tb[b * SP + b];
+                f2 sum = fmk(acc0.x + acc1.x, acc0.y + acc1.y);
+                sum.x += __shfl_xor_sync(0xffffffffu, sum.x, 1);
+                sum.y += __shfl_xor_sync(0xffffffffu, sum.y, 1);
+                sum.x += __shfl_xor_sync(0xffffffffu, sum.x, 2);
+                sum.y += __shfl_xor_sync(0xffffffffu, sum.y, 2);
+                if (valid && t4 == 0 && pr + a < br && qc + b < bc) {
+                    const f2 da = ga[a * SP + a], db = gb[b * SP + b];
                     const float dr = (da.x - sh) + (db.x - sh), di = da.y - db.y;   // A_aa + conj(B_bb)
                     const float inv = 1.0f / (dr * dr + di * di);
-                    const f2 v = fmk(Xs[pr + a][qc + b].x - acc.x, Xs[pr + a][qc + b].y - acc.y);
+                    const f2 v = fmk(Xs[pr + a][qc + b].x - sum.x, Xs[pr + a][qc + b].y - sum.y);
                     Xs[pr + a][qc + b] = fmk((v.x * dr + v.y * di) * inv, (v.y * dr - v.x * di) * inv);
                 }
-                __syncthreads();
+                group_sync(g);
             }
         }
+        __syncthreads();
     }
     // write back: complex128 block and the BF16 hi/lo planes of X (rows), lanes along q ...
     const long long ps = (long long)np * np;
@@ -209,7 +224,7 @@ __global__ void k_t_to_f32(const cplx* __restrict__ T, int n, float2* __restrict
     }
 }
 
-constexpr size_t LEAF_SMEM = sizeof(f2) * LB * PITCH + 2 * sizeof(f2) * SB * SP;
+constexpr size_t LEAF_SMEM = sizeof(f2) * LB * PITCH + 4 * 2 * sizeof(f2) * SB * SP;
 
 inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
@@ -225,6 +240,12 @@ int sylv_mixed_prepare(lb_handle_s* h, char* base, cudaStream_t s) {
     h->sylv = m;
     m->np = round_up(h->n, LB);
     m->nb = m->np / LB;
+    {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+            m->sms = sms;
+    }
     const size_t np = m->np;
     const size_t plane_bytes = 4 * np * np * sizeof(__nv_bfloat16);
     auto carve = [&](size_t bytes) {
@@ -282,8 +303,10 @@ int trisylv_mixed(lb_handle_s* h, cudaStream_t s, cplx* X, double shift) {
         const int hi = w < nb - 1 ? w : nb - 1;
         const int cnt = hi - lo + 1;
         if (w > 0) {
+            // a wave has at most nb blocks: split their K ranges so that the launch fills the SMs
             p.wave = w;
-            if (tc_gemm_launch(m->maps, p, cnt, 1, s)) return -1;
+            p.ksplit = std::max(1, std::min(8, m->sms / cnt));
+            if (tc_gemm_launch(m->maps, p, cnt, p.ksplit, s)) return -1;
         }
         k_sylv_leaf128<<<cnt, LEAF_THREADS, LEAF_SMEM, s>>>(m->Tf, m->Ttf, m->np, X, h->n, (float)shift, w, nb, m->Xp,
                                                              m->XTp, m->np);

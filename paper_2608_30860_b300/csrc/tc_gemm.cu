@@ -145,8 +145,25 @@ __global__ void __launch_bounds__(256, 1) k_tc_gemm(const __grid_constant__ Maps
         m0 = I * BM;
         n0 = J * BN;
     }
+    // K units (batch x BK block) of this CTA: all of them, or chunk blockIdx.y of ksplit (wavefront)
+    const bool split = p.wave >= 0 && p.ksplit > 1;
+    int u_lo = 0, u_hi = 0x7fffffff;
+    if (split) {
+        int units = 0;
+        for (int g = 0; g < p.nseg; ++g) units += seg_iters(cta_seg(p, g, I, J), 1);
+        u_lo = (int)((long long)units * blockIdx.y / p.ksplit);
+        u_hi = (int)((long long)units * (blockIdx.y + 1) / p.ksplit);
+    }
     int total_iters = 0;
-    for (int g = 0; g < p.nseg; ++g) total_iters += seg_iters(cta_seg(p, g, I, J), p.npairs);
+    {
+        int u = 0;
+        for (int g = 0; g < p.nseg; ++g) {
+            const int nu = seg_iters(cta_seg(p, g, I, J), 1);
+            const int lo = max(u, u_lo), hi = min(u + nu, u_hi);
+            if (hi > lo) total_iters += (hi - lo) * p.npairs;
+            u += nu;
+        }
+    }
     const uint32_t idesc_base = IDESC | ((uint32_t)p.fmt << 7) | ((uint32_t)p.fmt << 10);
 
     if (threadIdx.x == 0) {
@@ -170,7 +187,7 @@ __global__ void __launch_bounds__(256, 1) k_tc_gemm(const __grid_constant__ Maps
 
     if (warp == 0 && lane == 0) {
         // ---------------------------------------------------------------- TMA producer
-        int it = 0;
+        int it = 0, u = 0;
         bool ok = true;
         for (int g = 0; g < p.nseg && ok; ++g) {
             const Seg sg = cta_seg(p, g, I, J);
@@ -180,7 +197,8 @@ __global__ void __launch_bounds__(256, 1) k_tc_gemm(const __grid_constant__ Maps
             const CUtensorMap* bm = &maps.m[sg.b_map];
             for (int jb = 0; jb < sg.nbatch && ok; ++jb) {
                 const int aj = sg.a_j + jb * sg.a_jstep, bj = sg.b_j + jb * sg.b_jstep;
-                for (int kb = 0; kb < nkb && ok; ++kb) {
+                for (int kb = 0; kb < nkb && ok; ++kb, ++u) {
+                    if (u < u_lo || u >= u_hi) continue;
                     const int kc = sg.k0 + kb * BK;
                     for (int pr = 0; pr < p.npairs; ++pr, ++it) {
                         const int s = it % STAGES;
@@ -203,7 +221,7 @@ __global__ void __launch_bounds__(256, 1) k_tc_gemm(const __grid_constant__ Maps
             mbar_wait(full0 + 8 * (q % STAGES), (q / STAGES) & 1, p.err, 4);
     } else if (warp == 1 && lane == 0) {
         // ---------------------------------------------------------------- MMA issuer
-        int it = 0;
+        int it = 0, u = 0;
         bool ok = true;
         for (int g = 0; g < p.nseg && ok; ++g) {
             const Seg sg = cta_seg(p, g, I, J);
@@ -211,7 +229,10 @@ __global__ void __launch_bounds__(256, 1) k_tc_gemm(const __grid_constant__ Maps
             const uint32_t id_ii = (sg.sign == SIGN_NORMAL) ? (idesc_base | NEG_A) : idesc_base;
             const uint32_t id_ri = (sg.sign == SIGN_CONJ_B) ? (idesc_base | NEG_A) : idesc_base;
             const uint32_t id_ir = (sg.sign == SIGN_CONJ_A) ? (idesc_base | NEG_A) : idesc_base;
-            const int n_it = seg_iters(sg, p.npairs);
+            const int nu = seg_iters(sg, 1);
+            const int lo = max(u, u_lo) - u, hi = min(u + nu, u_hi) - u;
+            u += nu;
+            const int n_it = hi > lo ? (hi - lo) * p.npairs : 0;
             for (int q = 0; q < n_it; ++q, ++it) {
                 const int s = it % STAGES;
                 const uint32_t ph = (it / STAGES) & 1;
@@ -253,8 +274,13 @@ __global__ void __launch_bounds__(256, 1) k_tc_gemm(const __grid_constant__ Maps
                     const int col = n0 + c + t;
                     if (col < p.N) {
                         cplx v = cmake(sc * (double)__uint_as_float(vr[t]), sc * (double)__uint_as_float(vi[t]));
-                        if (p.accumulate) v = cadd(v, orow[col]);
-                        orow[col] = v;
+                        if (split) {
+                            atomicAdd(&orow[col].x, v.x);
+                            atomicAdd(&orow[col].y, v.y);
+                        } else {
+                            if (p.accumulate) v = cadd(v, orow[col]);
+                            orow[col] = v;
+                        }
                     }
                 }
             }

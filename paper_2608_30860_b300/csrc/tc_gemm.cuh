@@ -59,6 +59,9 @@ struct Params {
     // over K in [(I+1) BM, nb BM) and segment 1 over [(J+1) BN, nb BN)
     int wave;
     int nb;
+    // wavefront mode only: the K range of each block (both segments, in BK blocks) is split into
+    // ksplit chunks, chunk = blockIdx.y; partial products are added to out with FP64 atomics
+    int ksplit;
 };
 
 }  // namespace tc
