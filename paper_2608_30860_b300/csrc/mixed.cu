@@ -55,7 +55,7 @@ int mixed_prepare(lb_handle_s* h, cudaStream_t s) {
     m->Pp = reinterpret_cast<__half*>(carve(4 * (size_t)d * np * np * sizeof(__half)));
     m->sc = reinterpret_cast<double*>(carve(64 * sizeof(double)));
     // L~ planes with one scale for the whole stack
-    if (vec_norms(h->Lt, (long long)d * n * n, h->dpart, m->sc + 8, s)) return -1;
+    if (tc_maxabs(h->Lt, (long long)d * n * n, h->dpart, m->sc + 8, s)) return -1;
     if (tc_pick_scale(m->sc + 8, m->sc + 0, m->sc + 1, s)) return -1;
     if (tc_split_planes(h->Lt, n, n, n, 0, 0, m->sc + 0, m->Lp, (int)np, (long long)d * np * np, d,
                         (long long)n * n, (long long)np * np, s))
@@ -75,7 +75,7 @@ int jump_mixed(lb_handle_s* h, cudaStream_t s, const cplx* Z, cplx* Y, double al
     const int n = h->n, d = h->d, np = m->np;
     int* err = h->dinfo + 8;
     // pack Z^T (the B operand of product (1) is K-major: row c holds column c of Z)
-    if (vec_norms(Z, (long long)n * n, h->dpart, m->sc + 8, s)) return -1;
+    if (tc_maxabs(Z, (long long)n * n, h->dpart, m->sc + 8, s)) return -1;
     if (tc_pick_scale(m->sc + 8, m->sc + 2, m->sc + 3, s)) return -1;
     if (tc_split_planes(Z, n, n, n, 1, 0, m->sc + 2, m->Zp, np, (long long)np * np, 1, 0, (long long)np * np, s))
         return -1;
@@ -99,7 +99,7 @@ int jump_mixed(lb_handle_s* h, cudaStream_t s, const cplx* Z, cplx* Y, double al
     if (tc_gemm_launch(m->maps, p1, d * np / tc::BM, (n + tc::BN - 1) / tc::BN, s)) return -1;
     prof_end(h, s, 0, 8.0 * d * (double)n * n * n);
     // pack P_j (A operand of product (2), K-major rows as stored)
-    if (vec_norms(h->P, (long long)d * np * n, h->dpart, m->sc + 8, s)) return -1;
+    if (tc_maxabs(h->P, (long long)d * np * n, h->dpart, m->sc + 8, s)) return -1;
     if (tc_pick_scale(m->sc + 8, m->sc + 4, m->sc + 5, s)) return -1;
     if (tc_split_planes(h->P, n, np, n, 0, 0, m->sc + 4, m->Pp, np, (long long)d * np * np, d, (long long)np * n,
                         (long long)np * np, s))

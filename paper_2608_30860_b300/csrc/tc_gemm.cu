@@ -305,7 +305,7 @@ __global__ void k_split_planes(const cplx* __restrict__ X, long long ld_src, int
     __shared__ cplx tile[32][33];
     const int b = blockIdx.z;
     const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
-    const double sc = scale_dev ? scale_dev[0] : 1.0;
+    const float scf = scale_dev ? (float)scale_dev[0] : 1.0f;
     const cplx* Xb = X + (long long)b * src_bstride;
     // load the source tile so that global reads are coalesced
     for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
@@ -323,11 +323,12 @@ __global__ void k_split_planes(const cplx* __restrict__ X, long long ld_src, int
         const int r = r0 + yy, k = k0 + threadIdx.x;
         if (r >= rows_pad || k >= ld_dst) continue;
         cplx v = transpose ? tile[threadIdx.x][yy] : tile[yy][threadIdx.x];
-        if (conj) v.y = -v.y;
-        const double re = v.x * sc, im = v.y * sc;
-        const __half rh = __double2half(re), ih = __double2half(im);
-        const __half rl = __double2half(re - (double)__half2float(rh));
-        const __half il = __double2half(im - (double)__half2float(ih));
+        // the split works in FP32: the scale is a power of two and hi + lo keep 22 of FP32's 24 bits,
+        // so only the two conversions from FP64 use the (slow) FP64 pipe
+        const float re = (float)v.x * scf, im = (conj ? -(float)v.y : (float)v.y) * scf;
+        const __half rh = __float2half_rn(re), ih = __float2half_rn(im);
+        const __half rl = __float2half_rn(re - __half2float(rh));
+        const __half il = __float2half_rn(im - __half2float(ih));
         const long long o = (long long)b * dst_bstride + (long long)r * ld_dst + k;
         planes[o] = rh;
         planes[pstride + o] = rl;
@@ -367,6 +368,40 @@ __global__ void k_split_planes_bf16(const cplx* __restrict__ X, long long ld_src
 }
 
 // power-of-two scale with scale * maxabs <= 2^14
+// max over the entries of max(|re|, |im|) from the bit patterns (for non-negative IEEE doubles the
+// integer order is the numeric order), so no FP64 instruction is spent on it
+__global__ void __launch_bounds__(256) k_maxabs_part(const unsigned long long* __restrict__ x, long long len,
+                                                    unsigned long long* __restrict__ part) {
+    __shared__ unsigned long long red[8];
+    unsigned long long m = 0;
+    for (long long e = (long long)blockIdx.x * 256 + threadIdx.x; e < len; e += (long long)gridDim.x * 256) {
+        const unsigned long long b = __ldg(x + e) & 0x7fffffffffffffffull;
+        m = b > m ? b : m;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(0xffffffffu, m, o);
+        m = t > m ? t : m;
+    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < 8; ++q) m = red[q] > m ? red[q] : m;
+        part[blockIdx.x] = m;
+    }
+}
+
+__global__ void k_maxabs_final(const unsigned long long* __restrict__ part, int nblk, double* out) {
+    unsigned long long m = 0;
+    for (int b = threadIdx.x; b < nblk; b += 32) m = part[b] > m ? part[b] : m;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(0xffffffffu, m, o);
+        m = t > m ? t : m;
+    }
+    if (threadIdx.x == 0) out[0] = __longlong_as_double((long long)m);
+}
+
 __global__ void k_pick_scale(const double* maxabs, double* scale, double* inv) {
     if (threadIdx.x != 0) return;
     const double m = maxabs[0];
@@ -447,6 +482,15 @@ int tc_split_planes_bf16(const cplx* X, long long ld_src, int rows, int cols, in
     tc::k_split_planes_bf16<<<grid, dim3(32, 8), 0, s>>>(X, ld_src, rows, cols, transpose,
                                                           reinterpret_cast<__nv_bfloat16*>(planes), ld_dst, rows_pad,
                                                           pstride); lb_note_launch();
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int tc_maxabs(const cplx* X, long long len, double* part, double* out, cudaStream_t s) {
+    constexpr int blocks = 592;
+    tc::k_maxabs_part<<<blocks, 256, 0, s>>>(reinterpret_cast<const unsigned long long*>(X), 2 * len,
+                                             reinterpret_cast<unsigned long long*>(part)); lb_note_launch();
+    tc::k_maxabs_final<<<1, 32, 0, s>>>(reinterpret_cast<const unsigned long long*>(part), blocks, out);
+    lb_note_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -78,5 +78,7 @@ int tc_split_planes(const cplx* X, long long ld_src, int rows, int cols, int tra
 // the same packing into BF16 hi/lo planes, no scale
 int tc_split_planes_bf16(const cplx* X, long long ld_src, int rows, int cols, int transpose, void* planes,
                          int ld_dst, long long pstride, cudaStream_t s);
-// scale_dev[0] = 2^e with 2^e * maxabs <= 2^14 ; inv_dev[0] = 2^-e  (maxabs from vec_norms)
+// out[0] = max over the len complex entries of max(|re|, |im|); part: >= 592 doubles of scratch
+int tc_maxabs(const cplx* X, long long len, double* part, double* out, cudaStream_t s);
+// scale_dev[0] = 2^e with 2^e * maxabs <= 2^14 ; inv_dev[0] = 2^-e  (maxabs from tc_maxabs)
 int tc_pick_scale(const double* maxabs_dev, double* scale_dev, double* inv_dev, cudaStream_t s);
