@@ -278,6 +278,109 @@ __device__ void cta_trisylv(const C* T, C* X, int n, double s, C* sa, C* sb, C* 
     }
 }
 
+// barrier of one 128-thread group (named barriers 1, 2; 0 is __syncthreads)
+__device__ __forceinline__ void group_sync128(int g) { asm volatile("bar.sync %0, 128;" ::"r"(g + 1) : "memory"); }
+
+// The same blocked solve in complex64 with the blocks of one anti-diagonal shared by two 128-thread
+// groups (even and odd I), each with its own three staging tiles (tiles: 6 x GT x (GT + 1)):
+// 8 outputs per thread in the updates, 4 threads per entry in the 32 x 32 leaves.
+__device__ void cta_trisylv_c64(const float2* T, float2* X, int n, float2* tiles) {
+    constexpr int P = GT + 1;
+    const int g = threadIdx.x >> 7, lt = threadIdx.x & 127;
+    const int tx = lt & 31, ty = lt >> 5;
+    const int slot = lt >> 2, t4 = lt & 3;
+    float2* sa = tiles + g * 3 * GT * P;
+    float2* sb = sa + GT * P;
+    float2* sc = sb + GT * P;
+    const int nb = (n + GT - 1) / GT;
+    for (int S = 2 * nb - 2; S >= 0; --S) {
+        const int Ilo = max(0, S - (nb - 1)), Ihi = min(S, nb - 1);
+        for (int I = Ilo + g; I <= Ihi; I += 2) {
+            const int J = S - I;
+            const int r0 = I * GT, c0 = J * GT;
+            float2 acc[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) acc[i] = make_float2(0.f, 0.f);
+            for (int k0 = r0 + GT; k0 < n; k0 += GT) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int rr = ty + 4 * i;
+                    sa[rr * P + tx] = (r0 + rr < n && k0 + tx < n) ? T[(long long)(r0 + rr) * n + k0 + tx] : make_float2(0.f, 0.f);
+                    sb[rr * P + tx] = (k0 + rr < n && c0 + tx < n) ? X[(long long)(k0 + rr) * n + c0 + tx] : make_float2(0.f, 0.f);
+                }
+                group_sync128(g);
+#pragma unroll 4
+                for (int k = 0; k < GT; ++k) {
+                    const float2 bv = sb[k * P + tx];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) cf(acc[i], sa[(ty + 4 * i) * P + k], bv);
+                }
+                group_sync128(g);
+            }
+            for (int k0 = c0 + GT; k0 < n; k0 += GT) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int rr = ty + 4 * i;
+                    sa[rr * P + tx] = (r0 + rr < n && k0 + tx < n) ? X[(long long)(r0 + rr) * n + k0 + tx] : make_float2(0.f, 0.f);
+                    sb[tx * P + rr] = (c0 + rr < n && k0 + tx < n) ? cc(T[(long long)(c0 + rr) * n + k0 + tx]) : make_float2(0.f, 0.f);
+                }
+                group_sync128(g);
+#pragma unroll 4
+                for (int k = 0; k < GT; ++k) {
+                    const float2 bv = sb[k * P + tx];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) cf(acc[i], sa[(ty + 4 * i) * P + k], bv);
+                }
+                group_sync128(g);
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int rr = ty + 4 * i;
+                const bool in = r0 + rr < n && c0 + tx < n;
+                sc[rr * P + tx] = in ? cs(X[(long long)(r0 + rr) * n + c0 + tx], acc[i]) : make_float2(0.f, 0.f);
+                sa[rr * P + tx] = (r0 + rr < n && r0 + tx < n) ? T[(long long)(r0 + rr) * n + r0 + tx] : make_float2(0.f, 0.f);
+                sb[rr * P + tx] = (c0 + rr < n && c0 + tx < n) ? T[(long long)(c0 + rr) * n + c0 + tx] : make_float2(0.f, 0.f);
+            }
+            group_sync128(g);
+            for (int d = 2 * GT - 2; d >= 0; --d) {
+                const int alo = max(0, d - (GT - 1)), cnt = min(d, GT - 1) - alo + 1;
+                const bool valid = slot < cnt;
+                const int a = alo + slot, b = d - a;
+                float ax = 0.f, ay = 0.f;
+                if (valid) {
+                    for (int r = a + 1 + t4; r < GT; r += 4) {
+                        const float2 m = sa[a * P + r], x = sc[r * P + b];
+                        ax += m.x * x.x - m.y * x.y;
+                        ay += m.x * x.y + m.y * x.x;
+                    }
+                    for (int r = b + 1 + t4; r < GT; r += 4) {
+                        const float2 x = sc[a * P + r], m = sb[b * P + r];
+                        ax += x.x * m.x + x.y * m.y;
+                        ay += x.y * m.x - x.x * m.y;
+                    }
+                }
+                ax += __shfl_xor_sync(0xffffffffu, ax, 1);
+                ay += __shfl_xor_sync(0xffffffffu, ay, 1);
+                ax += __shfl_xor_sync(0xffffffffu, ax, 2);
+                ay += __shfl_xor_sync(0xffffffffu, ay, 2);
+                if (valid && t4 == 0 && r0 + a < n && c0 + b < n) {
+                    const float2 ta = sa[a * P + a], tb = sb[b * P + b];
+                    const float2 den = make_float2(ta.x + tb.x, ta.y - tb.y);
+                    sc[a * P + b] = cdv(cs(sc[a * P + b], make_float2(ax, ay)), den);
+                }
+                group_sync128(g);
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int rr = ty + 4 * i;
+                if (r0 + rr < n && c0 + tx < n) X[(long long)(r0 + rr) * n + c0 + tx] = sc[rr * P + tx];
+            }
+            group_sync128(g);
+        }
+        __syncthreads();
+    }
+}
+
 // complex Schur form of A (n x n, global, FP64) in place, unitary accumulated in Z (= Q):
 // Householder reduction to Hessenberg form, then implicitly shifted single-shift QR.
 // hv: n scratch (global); shared: red, sh (rotation / flags).  Returns 1 on a stall.
@@ -488,8 +591,7 @@ __device__ void phi32(const View& v, const float2* x, float2* w, Shared& sm) {
     const long long nn = (long long)v.n * v.n;
     for (long long e = threadIdx.x; e < nn; e += BT) v.Z1[e] = x[e];
     __syncthreads();
-    cta_trisylv(v.Tf, v.Z1, v.n, 0.0, reinterpret_cast<float2*>(sm.ga), reinterpret_cast<float2*>(sm.gb),
-                reinterpret_cast<float2*>(sm.gc));
+    cta_trisylv_c64(v.Tf, v.Z1, v.n, reinterpret_cast<float2*>(sm.ga));
     jump32(v, v.Z1, w, -1.f, sm);
 }
 
