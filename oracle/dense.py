@@ -108,6 +108,42 @@ def deflated_noJump_inverse(G, lam, c):
     return np.linalg.inv(lam * np.eye(n * n) - S_super(G) - c * deflation_term(n))
 
 
+# ----------------------------------------------------------------------------- single entries
+def _row_support(M, i):
+    nz = np.nonzero(M[i])[0]
+    return nz, M[i, nz]
+
+
+def jump_term_entries(Ls, X, pairs):
+    """Selected entries of K(X) = sum_j L_j X L_j^dag (Eq. (2)) straight from the definition,
+    K(X)_ab = sum_j sum_{k,l} L_j[a,k] X[k,l] conj(L_j[b,l]), summing over the nonzeros of rows a
+    and b of each L_j (cheap for sparse jumps stored dense, exact for any)."""
+    out = np.zeros(len(pairs), dtype=np.complex128)
+    for j, L in enumerate(Ls):
+        rows = {}
+        for t, (a, b) in enumerate(pairs):
+            for r in (a, b):
+                if r not in rows:
+                    rows[r] = _row_support(L, r)
+            ka, va = rows[a]
+            kb, vb = rows[b]
+            if len(ka) and len(kb):
+                out[t] += va @ X[np.ix_(ka, kb)] @ np.conj(vb)
+    return out
+
+
+def G_rows(H, Ls, idx):
+    """Rows idx of G = -iH - 1/2 sum_j L_j^dag L_j (Eq. (2)); (L^dag L)[a, :] = sum_m conj(L[m, a]) L[m, :]
+    over the nonzeros of column a of L."""
+    out = -1j * np.asarray(H[idx], dtype=np.complex128)
+    for L in Ls:
+        for t, a in enumerate(idx):
+            ms = np.nonzero(L[:, a])[0]
+            if len(ms):
+                out[t] -= 0.5 * (np.conj(L[ms, a]) @ L[ms])
+    return out
+
+
 # ----------------------------------------------------------------------------- steady state
 def hermitize_normalize(rho):
     r = 0.5 * (rho + dag(rho))

@@ -375,3 +375,19 @@ def test_tfim_conventions_and_reflection_symmetry():
     sz = [np.trace(P @ rho).real for P in dephase]
     assert np.allclose(sz, sz[::-1], atol=1e-12)
     assert np.linalg.eigvalsh(rho).min() > -1e-12
+
+
+def test_single_entry_jump_term_and_G_rows_match_dense():
+    """The entry-wise oracle (used at n = 4096) against the dense superoperator and G at small n,
+    for dense random jumps and for the sparse TFIM decay jumps."""
+    rng = np.random.default_rng(11)
+    for H, Ls in (gi.random_lindbladian(9, d=3, seed=5), gi.tfim(3, J=1.0, h=0.7, gamma=0.5, gamma_phi=0.1)):
+        n = H.shape[0]
+        X = gi.random_operator(n, seed=2)
+        KX = D.unvec(D.K_super(Ls) @ D.vec(X), n)
+        pairs = [(int(a), int(b)) for a, b in rng.integers(0, n, size=(25, 2))]
+        got = D.jump_term_entries(Ls, X, pairs)
+        ref = np.array([KX[a, b] for a, b in pairs])
+        assert np.abs(got - ref).max() < 1e-13 * max(1.0, np.abs(KX).max())
+        idx = [0, n - 1, n // 2]
+        assert np.abs(D.G_rows(H, Ls, idx) - D.G_matrix(H, Ls)[idx]).max() < 1e-13
