@@ -6,8 +6,10 @@ by the oracle from the definition (oracle.dense.jump_term_entries / G_rows: the 
 stored dense but have one nonzero per row and column), and (ii) properties that hold at any size,
 recomputed independently of the library: Phi is trace preserving and maps Hermitian to Hermitian
 (App. C), M(X) = -S^{-1} K(X) satisfies G W + W G^dag + K(X) = 0 (Eqs. (2)-(3)), and the refined
-steady state has ||L(rho)||_max < 1e-10 (torch FP64 matmuls).  Bars: 2e-5 for the split-FP16 jump
-term and 2e-3 for the mixed Sylvester solve, as in test_gpu_mixed.py; 1e-10 for the state.
+steady state has ||L(rho)||_max < 1e-10 (torch FP64 matmuls).  Bars: the jump term's second GEMM
+accumulates K = d n = 49152 products in FP32, so its bound (3 * 2^-22 + K * 2^-24) per GEMM, twice,
+is 5.9e-3 here (the n <= 512 tests of test_gpu_mixed.py use 2e-5 at K <= 2048; measured 3.6e-4 at
+n = 4096); 2e-3 for the mixed Sylvester solve, as in test_gpu_mixed.py; 1e-10 for the refined state.
 """
 import numpy as np
 import pytest
@@ -17,7 +19,8 @@ import lindblad_inputs as gi
 from oracle import dense as D
 
 pytestmark = pytest.mark.gpu
-TOL_JUMP = 2e-5
+N, D_JUMPS = 4096, 12
+TOL_JUMP = 2 * (3 * 2.0 ** -22 + D_JUMPS * N * 2.0 ** -24)
 TOL_SYLV = 2e-3
 
 
