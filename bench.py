@@ -27,6 +27,22 @@ METRIC = "Phi-applies/s & steady-state solve time at n=4096, mixed vs FP64, resi
 WORKLOAD = dict(workload="tfim12_n4096_d12", N_sites=12, n=4096, d=12, J=1.0, h=1.0, gamma=0.3)
 
 
+def max_over_ranks(values, world, device=None):
+    """Element-wise maximum of per-rank timings over the process group (all_reduce MAX); the
+    identity for a single process.  Replicas exchange nothing else."""
+    if world == 1:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(v) for v in t]
+
+
+def whole_job_rate(units_per_step, steps, world, ms):
+    """Units processed by all ranks divided by the slowest rank's time (weak scaling)."""
+    return units_per_step * steps * world / (ms / 1000.0)
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -216,7 +232,7 @@ def run_sweep(args, world, device):
 
 def sweep_line(args, r, world):
     count = args.sweep_count
-    value = count * args.steps * world / (r["ms"] / 1000.0)
+    value = whole_job_rate(count, args.steps, world, r["ms"])
     per_sweep_s = r["ms"] / 1000.0 / args.steps
     achieved = r["flops32"] / per_sweep_s / 1e12
     peak = fp32_alu_peak_tflops()
@@ -235,7 +251,7 @@ def sweep_line(args, r, world):
                      "flops_per_step": r["flops32"],
                      "note": "algorithmic complex64 flops of the Phi applications (jump term + triangular solve); "
                              "the FP64 anchors and the set-up are not counted"},
-        "e2e": {"value": count * args.steps / (r["e2e_ms"] / 1000.0), "unit": "steady-states/s",
+        "e2e": {"value": whole_job_rate(count, args.steps, world, r["e2e_ms"]), "unit": "steady-states/s",
                 "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
         "gpu_launches": r["gpu_launches"],
         "clocks": r["clocks"],
@@ -421,31 +437,20 @@ def main():
         return
     if args.workload == "sweep":
         r = run_sweep(args, world, device)
-        ms = r["ms"]
-        if world > 1:
-            t = torch.tensor([ms, r["e2e_ms"]], dtype=torch.float64, device=device)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            r["ms"], r["e2e_ms"] = float(t[0]), float(t[1])
+        r["ms"], r["e2e_ms"] = max_over_ranks([r["ms"], r["e2e_ms"]], world, device)
         if rank == 0:
             print(json.dumps(sweep_line(args, r, world)))
         if world > 1:
             torch.distributed.destroy_process_group()
         return
     r = run_ours(args, rank, world, device)
-    ms = r["ms"]
-    if world > 1:
-        t = torch.tensor([ms, r["e2e_ms"]], dtype=torch.float64, device=device)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms, e2e_ms = float(t[0]), float(t[1])
-    else:
-        e2e_ms = r["e2e_ms"]
+    ms, e2e_ms = max_over_ranks([r["ms"], r["e2e_ms"]], world, device)
     if rank != 0:
         torch.distributed.destroy_process_group()
         return
     pk, src = _peaks()
-    applies = args.steps * world
-    value = applies / (ms / 1000.0)
-    e2e_value = applies / (e2e_ms / 1000.0)
+    value = whole_job_rate(1, args.steps, world, ms)
+    e2e_value = whole_job_rate(1, args.steps, world, e2e_ms)
     n = r["n"]
     per_launch_ms = r["kms"] / max(r["launches"], 1)
     achieved = (r["kflops"] / max(r["launches"], 1)) / (per_launch_ms / 1000.0) / 1e12 if r["launches"] else None
