@@ -140,6 +140,10 @@ def cpu_baseline(n_sites=12, d_sample=1):
                        f"est. {per_apply:.1f} s per apply")}
 
 
+# DRAM bytes (read + write) per jump-term k_tc_gemm launch at n = 4096, d = 12, from one ncu capture
+# of the current kernel (mean of the two launches of an application)
+JUMP_GEMM_TRAFFIC_BYTES = (10165062144 + 3187236352 + 11702182656 + 238166528) / 2
+
 SWEEP = dict(workload="kerr_cat_sweep_1024", count=1024, seed=0, n_range=[16, 160], d=2,
              eps2=[1.0, 8.0], K=[0.5, 2.0], kappa1=[1e-3, 1e-1], kappa2=1.0)
 
@@ -470,7 +474,10 @@ def main():
                        l2="operands (1.6 GB L~ planes) exceed L2; no flush"),
         "roofline": {"bound": "tensor", "kernel": "k_tc_gemm (tcgen05 split-FP16 complex GEMM)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "frac": (achieved / peak) if achieved else None,
+                     "traffic": JUMP_GEMM_TRAFFIC_BYTES if args.sites == 12 else None,
+                     "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum per jump-term launch, "
+                                       "profiles/tc_gemm_traffic_tfim12_n4096.md",
                      "peak_source": f"bf16_tflops burst of {src} MEASURED_PEAKS.json (kind::f16 FP16 = BF16 rate)",
                      "launches": r["launches"], "ms_per_launch": per_launch_ms,
                      "flops_per_launch": r["kflops"] / max(r["launches"], 1)},

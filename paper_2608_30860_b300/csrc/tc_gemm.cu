@@ -138,6 +138,19 @@ __global__ void __launch_bounds__(256, 1) k_tc_gemm(const __grid_constant__ Maps
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN, I = 0, J = 0;
+    if (p.wave < 0) {
+        // grouped raster: consecutive CTAs walk a band of GROUP_M row tiles across all column tiles,
+        // so the ~148 resident CTAs share ~12 row tiles and ~12 column tiles of the operands in L2
+        // (with the plain x-fastest order every column tile re-read all of A from DRAM)
+        constexpr int GROUP_M = 12;
+        const int lin = blockIdx.y * gridDim.x + blockIdx.x;
+        const int per_group = GROUP_M * gridDim.y;
+        const int g0 = (lin / per_group) * GROUP_M;
+        const int gm = min(GROUP_M, (int)gridDim.x - g0);
+        const int local = lin % per_group;
+        m0 = (g0 + local % gm) * BM;
+        n0 = (local / gm) * BN;
+    }
     if (p.wave >= 0) {
         const int t = blockIdx.x + max(0, p.wave - (p.nb - 1));
         I = p.nb - 1 - t;
