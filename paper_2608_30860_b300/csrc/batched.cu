@@ -1049,6 +1049,28 @@ k_batched_solve(const Inst* __restrict__ insts, const int* __restrict__ order, i
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// the private stream, events and graph of one call, released on every return path (an unfinished
+// capture is ended and its graph dropped)
+struct CallResources {
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool capturing = false;
+    ~CallResources() {
+        if (capturing) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(cs, &g);
+            if (g) cudaGraphDestroy(g);
+        }
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (ev0) cudaEventDestroy(ev0);
+        if (ev1) cudaEventDestroy(ev1);
+        if (cs) cudaStreamDestroy(cs);
+    }
+};
+
 struct Plan {
     std::vector<Inst> insts;
     std::vector<int> order;
@@ -1129,17 +1151,16 @@ extern "C" lb_status steady_state_batched(int count, const int* n, int d, const 
     LB_CHECK_CUDA(cudaMemcpyAsync(d_inst, p.insts.data(), count * sizeof(bt::Inst), cudaMemcpyHostToDevice, user));
     LB_CHECK_CUDA(cudaMemcpyAsync(d_order, p.order.data(), count * sizeof(int), cudaMemcpyHostToDevice, user));
     // the launches run as one captured graph on a private stream ordered after the caller's stream
-    cudaStream_t cs;
-    cudaEvent_t ev0, ev1;
-    LB_CHECK_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    LB_CHECK_CUDA(cudaEventCreateWithFlags(&ev0, cudaEventDisableTiming));
-    LB_CHECK_CUDA(cudaEventCreateWithFlags(&ev1, cudaEventDisableTiming));
-    LB_CHECK_CUDA(cudaEventRecord(ev0, user));
-    LB_CHECK_CUDA(cudaStreamWaitEvent(cs, ev0, 0));
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
+    bt::CallResources r;
+    LB_CHECK_CUDA(cudaStreamCreateWithFlags(&r.cs, cudaStreamNonBlocking));
+    LB_CHECK_CUDA(cudaEventCreateWithFlags(&r.ev0, cudaEventDisableTiming));
+    LB_CHECK_CUDA(cudaEventCreateWithFlags(&r.ev1, cudaEventDisableTiming));
+    LB_CHECK_CUDA(cudaEventRecord(r.ev0, user));
+    LB_CHECK_CUDA(cudaStreamWaitEvent(r.cs, r.ev0, 0));
+    cudaStream_t cs = r.cs;
     LB_CHECK_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    cudaMemsetAsync(d_queue, 0, sizeof(int), cs);
+    r.capturing = true;
+    LB_CHECK_CUDA(cudaMemsetAsync(d_queue, 0, sizeof(int), cs));
     bt::k_batched_setup<<<count, bt::BT, smem, cs>>>(d_inst, count, d, (const cplx*)H_dev, (const cplx*)L_dev, a64,
                                                       a32, d_info);
     lb_note_launch();
@@ -1147,19 +1168,15 @@ extern "C" lb_status steady_state_batched(int count, const int* n, int d, const 
     bt::k_batched_solve<<<grid, bt::BT, smem, cs>>>(d_inst, d_order, count, d, (const cplx*)L_dev, (cplx*)rho_dev, a64, a32, d_queue,
                                                      o.tol, m, o.max_restarts, d_info);
     lb_note_launch();
-    LB_CHECK_CUDA(cudaStreamEndCapture(cs, &graph));
-    LB_CHECK_CUDA(cudaGraphInstantiate(&exec, graph, 0));
-    LB_CHECK_CUDA(cudaGraphLaunch(exec, cs));
-    LB_CHECK_CUDA(cudaEventRecord(ev1, cs));
-    LB_CHECK_CUDA(cudaStreamWaitEvent(user, ev1, 0));
+    r.capturing = false;
+    LB_CHECK_CUDA(cudaStreamEndCapture(cs, &r.graph));
+    LB_CHECK_CUDA(cudaGraphInstantiate(&r.exec, r.graph, 0));
+    LB_CHECK_CUDA(cudaGraphLaunch(r.exec, cs));
+    LB_CHECK_CUDA(cudaEventRecord(r.ev1, cs));
+    LB_CHECK_CUDA(cudaStreamWaitEvent(user, r.ev1, 0));
     std::vector<bt::InstInfo> hi(count);
     LB_CHECK_CUDA(cudaMemcpyAsync(hi.data(), d_info, count * sizeof(bt::InstInfo), cudaMemcpyDeviceToHost, user));
     LB_CHECK_CUDA(cudaStreamSynchronize(user));
-    cudaGraphExecDestroy(exec);
-    cudaGraphDestroy(graph);
-    cudaEventDestroy(ev0);
-    cudaEventDestroy(ev1);
-    cudaStreamDestroy(cs);
     const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     lb_status worst = LB_OK;
     for (int i = 0; i < count; ++i) {
@@ -1174,7 +1191,7 @@ extern "C" lb_status steady_state_batched(int count, const int* n, int d, const 
             inf.refine_steps = hi[i].refine_steps;
             inf.solve_ms = ms;
         }
-        if (hi[i].status < 0) worst = (lb_status)hi[i].status;
+        if (hi[i].status < 0 && worst >= 0) worst = (lb_status)hi[i].status;
         else if (hi[i].status > 0 && worst == LB_OK) worst = (lb_status)hi[i].status;
     }
     return worst;
