@@ -14,7 +14,10 @@
  *     leading dimension n.  A stack of d matrices is d*n*n contiguous elements.
  *   - Every pointer argument named *_dev is a DEVICE pointer owned by the caller.
  *     The library never frees caller memory and allocates no device memory of its
- *     own: everything it keeps lives in the caller-provided workspace.
+ *     own: everything it keeps lives in the caller-provided workspace.  The exceptions
+ *     are fixed and documented at their entry points: the 8 MiB scratch array of
+ *     lindbladian_apply_noalloc belongs to the library module, and steady_state_batched
+ *     creates (and releases) a private stream and a CUDA graph per call.
  *   - `stream` is a cudaStream_t passed as void*.  Calls are stream-ordered.  A call
  *     that returns solver results (steady_state, low_spectrum) synchronises the
  *     stream before returning, because its stopping test is read on the host once
