@@ -21,6 +21,12 @@ Systems (paper section / Eq. in brackets):
     L2 = sqrt(kappa nth) a^dag.
   * The qubit-decay example (footnote of Sec. 3.1) and the three-level cyclic
     example (Remark "Peripheral spectra of Phi").
+  * The memory-buffer cat qubit (App. B "Cat qubit", Table of its parameters):
+    H = g2 (a^2 b^dag + a^dag2 b) - eps_d (b + b^dag), four thermal jumps on the
+    memory a = a~ (x) I and the buffer b = I (x) b~, eps_d = g2 n_a / 5,
+    n_a = round(sqrt(3 n)), n_b = floor(n_a / 3).  Rates in units of 2 pi MHz.
+  * The stiff implicit-Euler family (Sec. 4.3 and App. B "Time evolution"): the
+    paper's dense random system plus K N^2 on H, N = diag(0, ..., n-1).
 """
 from __future__ import annotations
 
@@ -30,7 +36,8 @@ __all__ = [
     "ladder", "kerr_cat", "random_lindbladian", "paper_random_lindbladian",
     "tfim", "tfim_terms", "thermal_oscillator", "qubit_decay", "three_level_cycle",
     "haar_unitary", "conjugate_system", "random_operator", "random_hermitian",
-    "random_density", "kerr_cat_sweep", "CONFIGS",
+    "random_density", "kerr_cat_sweep", "memory_buffer_cat", "memory_buffer_dims",
+    "stiff_random_lindbladian", "CONFIGS",
 ]
 
 
@@ -218,6 +225,44 @@ def kerr_cat_sweep(count: int = 1024, seed: int = 0, nmin: int = 16, nmax: int =
         kappa1 = float(rng.uniform(1e-3, 1e-1))
         out.append(dict(n=n, eps2=eps2, K=K, kappa1=kappa1, kappa2=1.0))
     return out
+
+
+# App. B table (memory-buffer cat), in units of 2 pi MHz: g2/2pi = 0.763 MHz, kappa_b/2pi = 2.6 MHz,
+# kappa_a/2pi = 9.3 kHz, thermal occupations 10 % (memory) and 1.1 % (buffer).
+MEMORY_BUFFER = dict(g2=0.763, kappa_b=2.6, kappa_a=0.0093, nth_a=0.10, nth_b=0.011)
+
+
+def memory_buffer_dims(n: int):
+    """Truncations for a target dimension n (App. B): n_a = round(sqrt(3 n)), n_b = floor(n_a / 3)."""
+    na = int(round(np.sqrt(3.0 * n)))
+    nb = max(1, na // 3)
+    return na, nb
+
+
+def memory_buffer_cat(na: int, nb: int, g2: float = MEMORY_BUFFER["g2"], kappa_b: float = MEMORY_BUFFER["kappa_b"],
+                      kappa_a: float = MEMORY_BUFFER["kappa_a"], nth_a: float = MEMORY_BUFFER["nth_a"],
+                      nth_b: float = MEMORY_BUFFER["nth_b"], eps_d: float | None = None):
+    """Memory-buffer cat qubit of dimension n = na * nb; returns (H, [L1, L2, L3, L4]) with
+    L1 = sqrt(kb (1 + nb_th)) b, L2 = sqrt(kb nb_th) b^dag, L3 = sqrt(ka (1 + na_th)) a,
+    L4 = sqrt(ka na_th) a^dag; eps_d defaults to g2 na / 5 (cat size |alpha|^2 = na / 5)."""
+    if eps_d is None:
+        eps_d = g2 * na / 5.0
+    a = np.kron(ladder(na), np.eye(nb, dtype=np.complex128))
+    b = np.kron(np.eye(na, dtype=np.complex128), ladder(nb))
+    ad, bd = a.conj().T, b.conj().T
+    H = g2 * (a @ a @ bd + ad @ ad @ b) - eps_d * (b + bd)
+    H = 0.5 * (H + H.conj().T)
+    Ls = [np.sqrt(kappa_b * (1.0 + nth_b)) * b, np.sqrt(kappa_b * nth_b) * bd,
+          np.sqrt(kappa_a * (1.0 + nth_a)) * a, np.sqrt(kappa_a * nth_a) * ad]
+    return np.ascontiguousarray(H), [np.ascontiguousarray(L) for L in Ls]
+
+
+def stiff_random_lindbladian(n: int = 32, K: float = 0.0, seed: int = 0, gamma: float = 0.1):
+    """The implicit-Euler benchmark system: App. B's dense random family with K N^2 added to H."""
+    H, Ls = paper_random_lindbladian(n, seed=seed, gamma=gamma)
+    N = np.arange(n, dtype=np.float64)
+    H = H + np.diag(K * N ** 2).astype(np.complex128)
+    return np.ascontiguousarray(H), Ls
 
 
 # The five synthetic workloads: name -> (builder, kwargs, description).

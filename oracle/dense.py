@@ -193,6 +193,39 @@ def low_spectrum_with_vectors(H, Ls, k):
     return ev[order], [unvec(V[:, i], n) for i in order]
 
 
+# ----------------------------------------------------------------------------- gauge, resolvent, Euler
+def gauge_split(H, Ls, c):
+    """The gauge of Remark 'Non-uniqueness of the decomposition' (Eqs. lindblad_gauge and
+    lindblad_gauge_2): L~_j = L_j + c_j I and H~ = H + (1/2i) sum_j (c_j^* L~_j - c_j L~_j^dag).
+    The Lindbladian built from (H~, L~) is the same; its no-jump / jump split is not."""
+    n = H.shape[0]
+    I = np.eye(n, dtype=np.complex128)
+    Lt = [np.asarray(L, dtype=np.complex128) + cj * I for L, cj in zip(Ls, c)]
+    Ht = np.asarray(H, dtype=np.complex128) + sum(np.conj(cj) * L - cj * dag(L) for L, cj in zip(Lt, c)) / 2j
+    return Ht, Lt
+
+
+def resolvent_L(H, Ls, lam, B):
+    """R_lam^L(B) = (lam - L)^{-1}(B) by LU of the dense n^2 x n^2 matrix (Sec. 3.3, Corollary
+    'Resolvent of the Lindbladian'; the solve of the resolvent benchmarks, Sec. 3.4)."""
+    n = H.shape[0]
+    A = lam * np.eye(n * n, dtype=np.complex128) - liouvillian(H, Ls)
+    return unvec(sla.solve(A, vec(B)), n)
+
+
+def implicit_euler(H, Ls, rho0, dt, steps):
+    """Implicit Euler (Eq. resolvent, Sec. 4.3): rho_{t+dt} = (Id - dt L)^{-1} rho_t, the dense
+    n^2 x n^2 matrix factorised once; returns the states after each of the `steps` steps."""
+    n = H.shape[0]
+    A = np.eye(n * n, dtype=np.complex128) - dt * liouvillian(H, Ls)
+    lu = sla.lu_factor(A)
+    out, x = [], vec(np.asarray(rho0, dtype=np.complex128))
+    for _ in range(steps):
+        x = sla.lu_solve(lu, x)
+        out.append(unvec(x, n).copy())
+    return out
+
+
 # ----------------------------------------------------------------------------- adjoint gradient
 def steady_state_gradient(H_of_theta, Ls_of_theta, dL_super_of_theta, theta, O, eta=1.0):
     """Implicit differentiation of J = Tr(O rho_inf) (Remark 'Differentiating the steady state').

@@ -13,7 +13,12 @@ Contents (paper location):
   * System.precond          -- Alg. 2 (Sherman-Morrison deflated preconditioner).
   * arnoldi                 -- Arnoldi with full (two-pass) re-orthogonalisation.
   * steady_state_phi_arnoldi-- Alg. 4.
-  * steady_state_gmres      -- Alg. 3 (restarted right-preconditioned GMRES; no recycling).
+  * gcrodr                  -- right-preconditioned GMRES with Krylov subspace recycling
+                               (GCRO-DR of Parks, de Sturler, Mackey, Johnson and Maiti 2006,
+                               the recycling named in App. A.2).
+  * steady_state_gmres      -- Alg. 3 (restarted right-preconditioned GMRES, optionally recycled).
+  * resolvent_gmres         -- (lam - L) X = B with the preconditioner R_lam^S (Sec. 3.1, 3.4).
+  * implicit_euler_gmres    -- implicit Euler steps by the same solve at lam = 1/dt (Sec. 4.3).
   * low_spectrum_shift_invert -- Alg. 5 (shift-invert Arnoldi with thick restart).
 """
 from __future__ import annotations
@@ -242,9 +247,122 @@ def gmres_right(matvec, precond, b, x0, m=30, restarts=50, atol=1e-12, cycle_hoo
     return x
 
 
-def steady_state_gmres(sysm: System, tol=1e-10, m=20, restarts=50, eta=1.0):
+def _gs_qr(vectors):
+    """QR of a list of operators by Gram-Schmidt applied twice: (Q list, R upper triangular)."""
+    k = len(vectors)
+    Q, R = [], np.zeros((k, k), dtype=np.complex128)
+    for j, v in enumerate(vectors):
+        w = v.copy()
+        for _ in range(2):
+            for i, q in enumerate(Q):
+                h = hs_inner(q, w)
+                R[i, j] += h
+                w = w - h * q
+        R[j, j] = hs_norm(w)
+        Q.append(w / R[j, j])
+    return Q, R
+
+
+def _combine(basis, coeffs):
+    out = np.zeros_like(basis[0])
+    for c, v in zip(coeffs, basis):
+        out = out + c * v
+    return out
+
+
+def gcrodr(matvec, precond, b, x0, m=32, k=8, recycle=None, atol=0.0, max_cycles=50, cycle_hook=None):
+    """GCRO-DR(m, k) with right preconditioning (Parks et al. 2006; App. A.2's recycled GMRES).
+
+    Solves A x = b through the operator B = A P (x = x0 + P y).  A recycled pair (U, C) with
+    B U = C, C orthonormal, enters every cycle: the Arnoldi process runs on (I - C C^H) B for
+    m - k steps, giving B [U D, V_p] = [C, V_{p+1}] G with G = [[D, C^H B V_p], [0, Hbar]]
+    (D scales U to unit columns); y minimises ||[C, V_{p+1}]^H r - G y||.  After each cycle the
+    k harmonic Ritz vectors of B on range([U D, V_p]) with the smallest harmonic Ritz values,
+    i.e. G^H G z = theta G^H [C, V_{p+1}]^H [U D, V_p] z, become the new (U, C) (QR of G Z).
+    ``recycle`` = (U, C) of an earlier solve with the same operator (kept as is); the returned
+    pair is to be passed to the next solve.  ``cycle_hook(x)`` returning True stops early."""
+    x = np.array(x0, dtype=np.complex128)
+    r = b - matvec(x)
+    U = C = None
+    if recycle is not None and recycle[0]:
+        U = [u.copy() for u in recycle[0]]
+        C = [c.copy() for c in recycle[1]]
+        coef = [hs_inner(c, r) for c in C]
+        x = x + precond(_combine(U, coef))
+        r = r - _combine(C, coef)
+    cycles = steps = 0
+    while cycles < max_cycles:
+        beta = hs_norm(r)
+        if beta <= atol:
+            break
+        kk = len(U) if U else 0
+        p = m - kk
+        V = [r / beta]
+        Hb = np.zeros((p + 1, p), dtype=np.complex128)
+        Bm = np.zeros((kk, p), dtype=np.complex128)
+        done = p
+        for j in range(p):
+            w = matvec(precond(V[j]))
+            steps += 1
+            for _ in range(2):
+                for i in range(kk):
+                    h = hs_inner(C[i], w)
+                    Bm[i, j] += h
+                    w = w - h * C[i]
+                for i in range(j + 1):
+                    h = hs_inner(V[i], w)
+                    Hb[i, j] += h
+                    w = w - h * V[i]
+            hn = hs_norm(w)
+            Hb[j + 1, j] = hn
+            if hn <= 1e-14 * max(1.0, np.abs(Hb[: j + 1, j]).max()):
+                done = j + 1
+                V.append(np.zeros_like(w))
+                break
+            V.append(w / hn)
+        p = done
+        Hb, Bm, V = Hb[: p + 1, :p], Bm[:, :p], V[: p + 1]
+        dn = np.array([1.0 / hs_norm(u) for u in U]) if kk else np.zeros(0)
+        Ut = [u * dv for u, dv in zip(U, dn)] if kk else []
+        G = np.zeros((kk + p + 1, kk + p), dtype=np.complex128)
+        G[:kk, :kk] = np.diag(dn)
+        G[:kk, kk:] = Bm
+        G[kk:, kk:] = Hb
+        rhs = np.zeros(kk + p + 1, dtype=np.complex128)
+        rhs[kk] = beta
+        y, *_ = np.linalg.lstsq(G, rhs, rcond=None)
+        What = Ut + V[:p]
+        Vhat = (C if kk else []) + V
+        x = x + precond(_combine(What, y))
+        r = _combine(Vhat, rhs - G @ y)
+        cycles += 1
+        # new recycled pair from the harmonic Ritz vectors of smallest |theta|
+        F = np.zeros((kk + p + 1, kk + p), dtype=np.complex128)
+        for j in range(kk):
+            for i in range(kk):
+                F[i, j] = hs_inner(C[i], Ut[j])
+            for i in range(p + 1):
+                F[kk + i, j] = hs_inner(V[i], Ut[j])
+        F[kk:, kk:] = np.eye(p + 1, p)
+        theta, Z = sla.eig(G.conj().T @ G, G.conj().T @ F)
+        mag = np.where(np.isfinite(theta), np.abs(theta), np.inf)
+        keep = np.argsort(mag)[: min(k, kk + p)]
+        Z = Z[:, keep]
+        Y = [_combine(What, Z[:, t]) for t in range(Z.shape[1])]
+        GZ = G @ Z
+        Ct = [_combine(Vhat, GZ[:, t]) for t in range(Z.shape[1])]
+        C, R = _gs_qr(Ct)
+        Ri = np.linalg.inv(R)
+        U = [_combine(Y, Ri[:, t]) for t in range(len(Y))]
+        if cycle_hook is not None and cycle_hook(x):
+            break
+    return x, (U, C), dict(cycles=cycles, steps=steps, residual=hs_norm(r))
+
+
+def steady_state_gmres(sysm: System, tol=1e-10, m=20, restarts=50, eta=1.0, k_recycle=0):
     """Alg. 3: L~_eta rho = eta I by GMRES right-preconditioned with Precond(., 0, eta),
-    warm start |0><0|, test ||L(rho_hat)||_max < tol on the hermitised state each cycle."""
+    warm start |0><0|, test ||L(rho_hat)||_max < tol on the hermitised state each cycle.
+    k_recycle > 0 recycles that many harmonic Ritz vectors across restarts (App. A.2)."""
     n = sysm.n
     I = np.eye(n, dtype=np.complex128)
     x0 = np.zeros((n, n), dtype=np.complex128)
@@ -252,16 +370,69 @@ def steady_state_gmres(sysm: System, tol=1e-10, m=20, restarts=50, eta=1.0):
     # L~_eta rho = eta I  <=>  (0 - L~_eta) rho = -eta I
     mv = lambda X: sysm.shifted_deflated(X, 0.0, eta)
     pc = lambda X: sysm.precond(X, 0.0, eta)
-    state = {}
+    state = {"cycles": 0}
 
     def hook(x):
         rh = hermitize_normalize(x)
         res = float(np.abs(sysm.L(rh)).max())
         state["rho"], state["res"] = rh, res
+        state["cycles"] += 1
         return res < tol
 
-    gmres_right(mv, pc, -eta * I, x0, m=m, restarts=restarts, atol=0.0, cycle_hook=hook)
-    return state["rho"], dict(residual=state["res"])
+    if k_recycle > 0:
+        _, _, info = gcrodr(mv, pc, -eta * I, x0, m=m, k=k_recycle, atol=0.0, max_cycles=restarts, cycle_hook=hook)
+        state["steps"] = info["steps"]
+    else:
+        gmres_right(mv, pc, -eta * I, x0, m=m, restarts=restarts, atol=0.0, cycle_hook=hook)
+    return state["rho"], dict(residual=state["res"], cycles=state["cycles"], steps=state.get("steps"))
+
+
+def resolvent_gmres(sysm: System, lam, B, tol=1e-10, m=32, k_recycle=8, recycle=None, x0=None, max_cycles=50):
+    """(lam - L) X = B for lam > 0 by GMRES right-preconditioned with the no-jump resolvent R_lam^S
+    (Sec. 3.1: (lam - L) R_lam^S = Id - K R_lam^S), recycled (App. A.2).  The test of Sec. 3.4 /
+    App. B: for Hermitian B the iterate is hermitised and rescaled to its exact trace
+    Tr X = Tr B / lam, and the solve stops when ||(lam - L)(X_hat) - B||_max < tol.
+    Returns (X_hat, (U, C), info)."""
+    herm = np.abs(B - dag(B)).max() == 0.0
+    mv = lambda X: lam * X - sysm.L(X)
+    pc = lambda X: sysm.resolvent_S(X, lam)
+    target = np.trace(B) / lam
+    state = {}
+
+    def finish(x):
+        xh = 0.5 * (x + dag(x)) if herm else x
+        tr = np.trace(xh)
+        if abs(tr) > 0:
+            xh = xh * (target / tr)
+        return xh
+
+    def hook(x):
+        xh = finish(x)
+        res = float(np.abs(mv(xh) - B).max())
+        state["x"], state["res"] = xh, res
+        return res < tol
+
+    x0 = np.zeros_like(B) if x0 is None else x0
+    if hook(x0):
+        return state["x"], recycle, dict(residual=state["res"], cycles=0, steps=0)
+    x, rec, info = gcrodr(mv, pc, B, x0, m=m, k=k_recycle, recycle=recycle, atol=0.0, max_cycles=max_cycles,
+                          cycle_hook=hook)
+    return state["x"], rec, dict(residual=state["res"], cycles=info["cycles"], steps=info["steps"])
+
+
+def implicit_euler_gmres(sysm: System, rho0, dt, steps, tol=1e-10, m=32, k_recycle=8):
+    """Implicit Euler (Eq. resolvent, Sec. 4.3): each step solves (1/dt - L) rho_{t+dt} = rho_t / dt
+    with the preconditioner R_{1/dt}^S, warm-started from rho_t, the recycled subspace carried from
+    step to step (one operator for all steps).  Each solve stops when the max-norm residual is below
+    tol * ||rho_t / dt||_max.  Returns the list of states."""
+    lam = 1.0 / dt
+    out, rho, rec = [], np.array(rho0, dtype=np.complex128), None
+    for _ in range(steps):
+        B = rho * lam
+        rho, rec, _ = resolvent_gmres(sysm, lam, B, tol=tol * np.abs(B).max(), m=m, k_recycle=k_recycle,
+                                      recycle=rec, x0=rho)
+        out.append(rho.copy())
+    return out
 
 
 # ----------------------------------------------------------------------------- shift-invert

@@ -117,8 +117,7 @@ def test_three_level_gauge_shift(golden):
     kv, _ = golden("three_level_gauge.txt")
     H, Ls = gi.three_level_cycle()
     c = kv["c"]
-    Lt = [L + cj * np.eye(3) for L, cj in zip(Ls, c)]
-    Ht = H + sum((np.conj(cj) * L - cj * L.conj().T) for L, cj in zip(Lt, c)) / 2j
+    Ht, Lt = D.gauge_split(H, Ls, c)
     # the gauge leaves L unchanged (Eq. lindblad_gauge_split)
     assert np.abs(D.liouvillian(Ht, Lt) - D.liouvillian(H, Ls)).max() < 1e-14
     ev = np.linalg.eigvals(D.Phi_super(Ht, Lt))
@@ -391,3 +390,178 @@ def test_single_entry_jump_term_and_G_rows_match_dense():
         assert np.abs(got - ref).max() < 1e-13 * max(1.0, np.abs(KX).max())
         idx = [0, n - 1, n // 2]
         assert np.abs(D.G_rows(H, Ls, idx) - D.G_matrix(H, Ls)[idx]).max() < 1e-13
+
+
+# ----------------------------------------------------------------------------- adjoint, vectors
+def test_L_adjoint_is_the_hilbert_schmidt_adjoint():
+    """System.L_adjoint against the conjugate transpose of the dense Liouvillian and the defining
+    identity <Y, L(X)> = <L^*(Y), X> (a dropped G term or a swapped dagger fails both)."""
+    H, Ls = gi.random_lindbladian(6, d=3, seed=2)
+    s = K.System(H, Ls)
+    X, Y = gi.random_operator(6, seed=3), gi.random_operator(6, seed=4)
+    ref = D.unvec(D.liouvillian(H, Ls).conj().T @ D.vec(Y), 6)
+    assert np.abs(s.L_adjoint(Y) - ref).max() < 1e-13
+    assert abs(K.hs_inner(Y, s.L(X)) - K.hs_inner(s.L_adjoint(Y), X)) < 1e-12
+    # L^* is unital: L^*(I) = 0 (trace preservation of the dynamics)
+    assert np.abs(s.L_adjoint(np.eye(6, dtype=np.complex128))).max() < 1e-13
+
+
+def test_low_spectrum_with_vectors_damped_oscillator():
+    """The damped oscillator at n_th = 0 has the exact truncated spectrum -kappa(p+q)/2 + i omega(q-p)
+    (triangular in the excitation number): values and eigenvectors (L v = lambda v) are checked."""
+    n, omega, kappa = 7, 1.0, 1.0
+    H, Ls = gi.thermal_oscillator(n, omega=omega, kappa=kappa, nth=0.0)
+    lam, vecs = D.low_spectrum_with_vectors(H, Ls, 3)
+    full = np.array([-kappa * (p + q) / 2 + 1j * omega * (q - p) for p in range(n) for q in range(n)])
+    full = full[np.argsort(np.abs(full))]
+    ref = full[1:4]          # -1 and the pair -1/2 +- i; the next modulus (2) is well separated
+    assert np.abs(np.abs(full[4]) - np.abs(full[3])) > 0.5
+    assert _same_multiset(lam, ref, 1e-10)
+    Lmat = D.liouvillian(H, Ls)
+    for l, v in zip(lam, vecs):
+        r = D.unvec(Lmat @ D.vec(v), n) - l * v
+        assert np.abs(r).max() < 1e-10 * np.abs(v).max()
+        assert abs(np.trace(v)) < 1e-10 * np.abs(v).max() * n
+
+
+# ----------------------------------------------------------------------------- gauge split
+def test_gauge_split_keeps_L_and_moves_B_into_the_jump_part():
+    """Eq. lindblad_gauge_split on a random system: L unchanged, G~ = G - B - 1/2 sum |c_j|^2 with
+    B = sum c_j^* L_j, and K~ Kraus (K~ - K = B rho + rho B^dag + sum |c_j|^2 rho)."""
+    H, Ls = gi.random_lindbladian(5, d=3, seed=9)
+    c = np.array([0.3 - 0.2j, -0.7 + 0.1j, 0.25j])
+    Ht, Lt = D.gauge_split(H, Ls, c)
+    assert np.abs(Ht - Ht.conj().T).max() < 1e-14
+    assert np.abs(D.liouvillian(Ht, Lt) - D.liouvillian(H, Ls)).max() < 1e-13
+    Bm = sum(np.conj(cj) * L for cj, L in zip(c, Ls))
+    Gt = D.G_matrix(Ht, Lt)
+    assert np.abs(Gt - (D.G_matrix(H, Ls) - Bm - 0.5 * np.sum(np.abs(c) ** 2) * np.eye(5))).max() < 1e-13
+    X = gi.random_operator(5, seed=1)
+    dK = D.unvec((D.K_super(Lt) - D.K_super(Ls)) @ D.vec(X), 5)
+    assert np.abs(dK - (Bm @ X + X @ Bm.conj().T + np.sum(np.abs(c) ** 2) * X)).max() < 1e-13
+
+
+# ----------------------------------------------------------------------------- resolvent of L
+@pytest.mark.parametrize("lam", [2.0, 0.3])
+def test_resolvent_L_neumann_series_trace_and_laplace(rand6, lam):
+    """Corollary 'Resolvent of the Lindbladian': R_lam^L = R_lam^S sum_k (K R_lam^S)^k (a truncated
+    series, independent of the LU); Tr R_lam^L(B) = Tr B / lam; and the Laplace transform
+    R_lam^L(B) = int_0^inf e^{-lam t} e^{L t} B dt by quadrature."""
+    H, Ls = rand6
+    n = 6
+    B = gi.random_hermitian(n, seed=5)
+    X = D.resolvent_L(H, Ls, lam, B)
+    RS = D.resolvent_S(D.G_matrix(H, Ls), lam)
+    N = D.K_super(Ls) @ RS
+    acc, term = np.zeros(n * n, dtype=np.complex128), D.vec(B).astype(np.complex128)
+    for _ in range(4000):
+        acc = acc + term
+        term = N @ term
+        if np.abs(term).max() < 1e-17:
+            break
+    assert np.abs(D.unvec(RS @ acc, n) - X).max() < 1e-11 * np.abs(X).max()
+    assert abs(np.trace(X) - np.trace(B) / lam) < 1e-12 * abs(np.trace(B) / lam)
+    Lm = D.liouvillian(H, Ls)
+    f = lambda t: np.exp(-lam * t) * (sla.expm(Lm * t) @ D.vec(B))
+    lap, _ = quad_vec(f, 0.0, np.inf, epsabs=1e-12, epsrel=1e-11)
+    assert np.abs(D.unvec(lap, n) - X).max() < 1e-8 * np.abs(X).max()
+
+
+# ----------------------------------------------------------------------------- implicit Euler
+def test_implicit_euler_eigenvector_exact_and_first_order():
+    """Eq. resolvent: an eigenvector v (L v = lambda v) evolves exactly as (1 - dt lambda)^-k v; the
+    trace is kept at every step; and the error against e^{L t} rho0 halves with dt (first order)."""
+    H, Ls = gi.random_lindbladian(5, d=2, seed=3)
+    lam, vecs = D.low_spectrum_with_vectors(H, Ls, 1)
+    v = vecs[0]
+    dt, k = 0.3, 4
+    out = D.implicit_euler(H, Ls, v, dt, k)
+    assert np.abs(out[-1] - v * (1 - dt * lam[0]) ** (-k)).max() < 1e-12 * np.abs(v).max()
+    rho0 = gi.random_density(5, seed=2)
+    T = 1.0
+    exact = D.unvec(sla.expm(D.liouvillian(H, Ls) * T) @ D.vec(rho0), 5)
+    errs = []
+    for steps in (20, 40, 80):
+        traj = D.implicit_euler(H, Ls, rho0, T / steps, steps)
+        assert all(abs(np.trace(r) - 1.0) < 1e-12 for r in traj)
+        errs.append(np.abs(traj[-1] - exact).max())
+    assert 1.8 < errs[0] / errs[1] < 2.2 and 1.8 < errs[1] / errs[2] < 2.2
+
+
+# ----------------------------------------------------------------------------- recycled GMRES
+def test_gcrodr_solves_and_keeps_its_recycled_relation():
+    """GCRO-DR on a small shifted system: the solution equals the dense solve, the returned pair
+    satisfies B U = C with C orthonormal, and a second right-hand side solved with that pair needs
+    fewer matrix-vector products than a solve without it."""
+    H, Ls = gi.random_lindbladian(8, d=3, seed=6)
+    s = K.System(H, Ls)
+    lam = 0.05
+    mv = lambda X: lam * X - s.L(X)
+    pc = lambda X: s.resolvent_S(X, lam)
+    b1, b2 = gi.random_operator(8, seed=1), gi.random_operator(8, seed=2)
+    x1, (U, C), info1 = K.gcrodr(mv, pc, b1, np.zeros_like(b1), m=12, k=4, atol=1e-13, max_cycles=60)
+    ref = D.resolvent_L(H, Ls, lam, b1)
+    assert np.abs(x1 - ref).max() < 1e-10 * np.abs(ref).max()
+    Gm = np.array([[K.hs_inner(a, c) for c in C] for a in C])
+    assert np.abs(Gm - np.eye(len(C))).max() < 1e-12
+    for u, c in zip(U, C):
+        assert np.abs(mv(pc(u)) - c).max() < 1e-10
+    _, _, cold = K.gcrodr(mv, pc, b2, np.zeros_like(b2), m=12, k=4, atol=1e-11, max_cycles=60)
+    x2, _, warm = K.gcrodr(mv, pc, b2, np.zeros_like(b2), m=12, k=4, recycle=(U, C), atol=1e-11, max_cycles=60)
+    assert np.abs(x2 - D.resolvent_L(H, Ls, lam, b2)).max() < 1e-9 * np.abs(x2).max()
+    assert warm["steps"] < cold["steps"]
+
+
+@pytest.mark.parametrize("make", [lambda: gi.kerr_cat(14), lambda: gi.random_lindbladian(9, d=3, seed=4)])
+def test_tierb_alg3_recycled_matches_lu(make):
+    H, Ls = make()
+    rho, info = K.steady_state_gmres(K.System(H, Ls), tol=1e-12, m=16, k_recycle=4)
+    ref = D.steady_state_lu(H, Ls)
+    assert info["residual"] < 1e-12
+    assert np.linalg.norm(rho - ref) / np.linalg.norm(ref) < 1e-9
+
+
+def test_tierb_resolvent_gmres_matches_dense_at_three_shifts():
+    """The resolvent benchmark's solve (Sec. 3.4): B = I/n, lam = lam_max 10^{0,-1,-2}."""
+    H, Ls = gi.paper_random_lindbladian(7, seed=0)
+    s = K.System(H, Ls)
+    lmax = np.abs(D.liouvillian_eigenvalues(H, Ls)).max()
+    B = np.eye(7, dtype=np.complex128) / 7
+    rec = None
+    for lam in (lmax, lmax / 10, lmax / 100):
+        X, rec, info = K.resolvent_gmres(s, lam, B, tol=1e-12, m=16, k_recycle=4)
+        ref = D.resolvent_L(H, Ls, lam, B)
+        assert info["residual"] < 1e-12
+        assert np.abs(X - ref).max() < 1e-10 * np.abs(ref).max()
+        rec = None   # each shift is another operator
+
+
+def test_tierb_implicit_euler_gmres_matches_dense():
+    H, Ls = gi.stiff_random_lindbladian(8, K=2.0, seed=1)
+    rho0 = np.zeros((8, 8), dtype=np.complex128)
+    rho0[0, 0] = 1.0
+    dt = 0.05
+    ref = D.implicit_euler(H, Ls, rho0, dt, 6)
+    got = K.implicit_euler_gmres(K.System(H, Ls), rho0, dt, 6, tol=1e-12, m=12, k_recycle=4)
+    for a, b in zip(got, ref):
+        assert np.abs(a - b).max() < 1e-10
+
+
+def test_memory_buffer_cat_generator():
+    """App. B cat qubit: a = a~ (x) I and b = I (x) b~ commute, the truncations follow
+    n_a = round(sqrt(3 n)), n_b = floor(n_a / 3), S is invertible (case 2 of Theorem 1) and the
+    steady state is unique (LU and SVD null vectors agree)."""
+    assert gi.memory_buffer_dims(64) == (14, 4)
+    na, nb = 6, 2
+    H, Ls = gi.memory_buffer_cat(na, nb)
+    n = na * nb
+    assert H.shape == (n, n) and len(Ls) == 4
+    b, a = Ls[0], Ls[2]
+    assert np.abs(a @ b - b @ a).max() < 1e-14
+    assert np.abs(a @ b.conj().T - b.conj().T @ a).max() < 1e-14
+    G = D.G_matrix(H, Ls)
+    assert np.abs(np.linalg.eigvals(G).real).min() > 1e-6
+    r_lu = D.steady_state_lu(H, Ls)
+    r_svd, sv = D.steady_state_svd(H, Ls)
+    assert sv[-2] > 1e3 * sv[-1]
+    assert np.abs(r_lu - r_svd).max() < 1e-9
