@@ -47,7 +47,8 @@ typedef enum {
                                   Eq. ShermanMorr / Alg. 2 is undefined */
     LB_WORKSPACE_TOO_SMALL = -4,
     LB_NOT_IMPLEMENTED = -5,
-    LB_SOLVER_ERROR = -6       /* a factorisation in set-up failed (info != 0) */
+    LB_SOLVER_ERROR = -6       /* a factorisation in set-up failed (info != 0), or the Schur form failed
+                                  its backward-error gate (lb_opts.schur_tol) */
 } lb_status;
 
 typedef enum {
@@ -80,6 +81,18 @@ typedef struct {
                              set-up */
     double eig_cond_max;  /* cond(U) gate of the eigenbasis route (default 1e3): the route is used only if
                              ||R||_F ||R^{-1}||_F / n <= eig_cond_max, R = Q^dag U */
+    double schur_tol;     /* set-up gate on the Schur form (default 1e-12): lindblad_setup fails with
+                             LB_SOLVER_ERROR when ||strictly-lower(Q^dag G Q)||_F / ||G||_F exceeds it.  A
+                             backward error e makes T the Schur factor of G + E, ||E||_F = e ||G||_F, and the
+                             FP64 Phi path then stagnates near ||L rho||_max ~ 2 e ||G||_F ||rho||_2; the
+                             refined (mixed) solves absorb it as a preconditioner error */
+    int    recycle_k;     /* harmonic Ritz vectors kept by the recycled GMRES (App. A.2; default 8, 0 = plain
+                             restarted GMRES); at most 16 and at most gmres_m - 2; read at set-up (workspace) */
+    const double* gauge_c;/* nullable host array of d complex shifts (re, im pairs): the gauge of Remark
+                             "Non-uniqueness of the decomposition", L~_j = L_j + c_j I and
+                             H~ = H + (1/2i) sum_j (c_j^* L~_j - c_j L~_j^dag); read by lindblad_setup only.
+                             L is unchanged; the split S~ + K~ (and so Phi, the preconditioners and the
+                             Schur form) is that of (H~, L~).  NULL = the split of Eq. (2) */
 } lb_opts;
 
 /* Lyapunov route: Bartels-Stewart on the Schur form (App. A.1.1), or the eigenbasis divide of Alg. 1
@@ -124,8 +137,9 @@ size_t lindblad_workspace_bytes(int n, int d, const lb_opts* opts);
  * R^{-1} for the eigenbasis route and applies the cond(U) gate.  On success *out receives a handle.
  * Returns LB_OK, or LB_ILL_CONDITIONED (handle valid, Schur route in use) when LB_ROUTE_EIG was
  * requested and the gate refused it.  Errors: LB_INVALID_ARG (n < 2, d < 1, null pointers),
- * LB_WORKSPACE_TOO_SMALL, LB_SOLVER_ERROR, LB_CUDA_ERROR.  info (nullable) receives set-up
- * diagnostics. */
+ * LB_WORKSPACE_TOO_SMALL, LB_SOLVER_ERROR (a factorisation failed, or the Schur backward error
+ * exceeds opts->schur_tol; info->schur_backward_err then carries the measured value and no handle
+ * is returned), LB_CUDA_ERROR.  info (nullable) receives set-up diagnostics. */
 lb_status lindblad_setup(const void* H_dev, const void* L_dev, int n, int d,
                          void* workspace_dev, size_t workspace_bytes, void* stream,
                          const lb_opts* opts, lindblad_handle* out, lb_info* info);

@@ -1138,13 +1138,9 @@ extern "C" lb_status steady_state_batched(int count, const int* n, int d, const 
     float2* a32 = reinterpret_cast<float2*>(ws + p.off32);
     cudaStream_t user = (cudaStream_t)stream;
     const auto t0 = std::chrono::steady_clock::now();
-    static bool attr = false;
     const int smem = (int)sizeof(bt::Shared);
-    if (!attr) {
-        LB_CHECK_CUDA(cudaFuncSetAttribute(bt::k_batched_setup, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        LB_CHECK_CUDA(cudaFuncSetAttribute(bt::k_batched_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        attr = true;
-    }
+    if (lb_smem_attr((const void*)bt::k_batched_setup, smem) || lb_smem_attr((const void*)bt::k_batched_solve, smem))
+        return LB_CUDA_ERROR;
     int dev = 0, nsm = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);

@@ -59,3 +59,7 @@ int zgemm_f64(const ZGemmArgs& a, cudaStream_t s);
 
 // counts every kernel launch issued by the library (lb_launch_count in the C ABI)
 void lb_note_launch();
+
+// raises a kernel's dynamic shared-memory limit on the current device, once per (kernel, device);
+// thread-safe; returns 0 on success
+int lb_smem_attr(const void* kernel, int bytes);

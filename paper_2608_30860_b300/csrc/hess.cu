@@ -38,12 +38,7 @@ int small_schur(const cplx* A, int lda, int m, int hess_in, int order, int nsel,
                 cplx* Tout, cplx* Zout, int* info, cudaStream_t s) {
     if (m < 1 || m > 64) return -1;
     size_t smem = 3 * (size_t)m * (m + 1) * sizeof(cplx);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_small_schur, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             3 * 64 * 65 * (int)sizeof(cplx));
-        attr = true;
-    }
+    if (lb_smem_attr((const void*)k_small_schur, 3 * 64 * 65 * (int)sizeof(cplx))) return -1;
     k_small_schur<<<1, 32, smem, s>>>(A, lda, m, hess_in, order, nsel, evals, evecs, Tout, Zout, info); lb_note_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

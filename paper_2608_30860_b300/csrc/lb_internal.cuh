@@ -33,6 +33,9 @@ struct lb_handle_s {
     cplx* P = nullptr;                 // d n^2 scratch (jump-term intermediate)
     cplx* X[NSCRATCH] = {};            // n x n scratch
     cplx* best = nullptr;              // n x n
+    cplx* Rres = nullptr;              // L(rho) of the accepted steady-state iterate (original basis)
+    cplx* bk0 = nullptr;               // backups of the accepted iterate during refinement
+    cplx* bk1 = nullptr;
     cplx* W = nullptr;                 // R_mu^S(I) for the Sherman-Morrison preconditioner
     cplx* Wa = nullptr;                // its adjoint counterpart R_mu^{S*}(I)
     cplx* Ua = nullptr;                // J T^dag J (J = index reversal): upper triangular, adjoint solves

@@ -6,6 +6,9 @@
 
 #include <algorithm>
 #include <atomic>
+#include <mutex>
+#include <set>
+#include <tuple>
 #include <chrono>
 #include <cmath>
 #include <complex>
@@ -77,6 +80,9 @@ void layout(lb_handle_s* h, char* base, int n, int d, const lb_opts* o, size_t s
     h->P = c.take<cplx>(std::max((size_t)d * nn, mixed_P_rows(n, d) * (size_t)n));
     for (int i = 0; i < NSCRATCH; ++i) h->X[i] = c.take<cplx>(nn);
     h->best = c.take<cplx>(nn);
+    h->Rres = c.take<cplx>(nn);
+    h->bk0 = c.take<cplx>(nn);
+    h->bk1 = c.take<cplx>(nn);
     h->W = c.take<cplx>(nn);
     h->Wa = c.take<cplx>(nn);
     h->Ua = c.take<cplx>(nn);
@@ -109,6 +115,20 @@ void layout(lb_handle_s* h, char* base, int n, int d, const lb_opts* o, size_t s
 // ============================================================================ launch counter
 static std::atomic<long long> g_launches{0};
 void lb_note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// cudaFuncSetAttribute applies per device: remember (kernel, device, bytes) pairs already raised
+int lb_smem_attr(const void* kernel, int bytes) {
+    static std::mutex mu;
+    static std::set<std::tuple<const void*, int, int>> done;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+    std::lock_guard<std::mutex> lock(mu);
+    auto key = std::make_tuple(kernel, dev, bytes);
+    if (done.count(key)) return 0;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) return -1;
+    done.insert(key);
+    return 0;
+}
 
 // ============================================================================ kernel timing
 void prof_begin(lb_handle_s* h, cudaStream_t s, int kid) {
@@ -230,14 +250,17 @@ int phi_schur(lb_handle_s* h, cudaStream_t s, const cplx* X, cplx* Y, int form, 
 // ============================================================================ Arnoldi
 // One Arnoldi cycle of length up to m on op, starting from V[0] (unit norm).  Classical
 // Gram-Schmidt applied twice per step; the Hessenberg column lives on the device
-// (column-major, leading dimension ldh) and only the new subdiagonal entry is read back to
-// detect breakdown.  Returns the number of completed steps in *k_out.
+// (column-major, leading dimension ldh).  Breakdown is detected on the device (the step is
+// recorded and the later basis vectors are zero), so the host synchronises once per cycle, not
+// once per step.  Returns the number of completed steps in *k_out.
 int arnoldi_cycle(lb_handle_s* h, cudaStream_t s, cplx* basis, cplx* hess, int j0, int m, const OpFn& op,
                   int* k_out) {
     const long long nn = (long long)h->n * h->n;
     cplx* hc2 = h->small;
     cplx* nrm2 = h->small + (KMAX + 2);
     cplx* inv = h->small + 2 * (KMAX + 2);
+    int* brk = h->dinfo + 12;
+    LB_CHECK_CUDA(cudaMemsetAsync(brk, 0, sizeof(int), s));
     for (int k = j0; k < m; ++k) {
         cplx* w = basis + (k + 1) * nn;
         cplx* hcol = hess + (size_t)k * h->ldh;
@@ -248,17 +271,13 @@ int arnoldi_cycle(lb_handle_s* h, cudaStream_t s, cplx* basis, cplx* hess, int j
             if (vec_gemv(w, basis, nn, k + 1, out, nn, -1.0, 1, s)) return -1;
         }
         if (vec_dot_block(w, nn, 1, w, nn, nrm2, h->part, 0, s)) return -1;
-        if (vec_finish_column(hcol, hc2, k + 1, nrm2, inv, s)) return -1;
-        cplx hk[KMAX + 2];
-        LB_CHECK_CUDA(cudaMemcpyAsync(hk, hcol, (k + 2) * sizeof(cplx), cudaMemcpyDeviceToHost, s));
-        LB_CHECK_CUDA(cudaStreamSynchronize(s));
-        double hmax = 0.0;
-        for (int i = 0; i <= k; ++i) hmax = std::max(hmax, std::hypot(hk[i].x, hk[i].y));
-        double beta = hk[k + 1].x;
-        if (!(beta > 1e-13 * std::max(1.0, hmax))) { *k_out = k + 1; return 0; }
+        if (vec_finish_column(hcol, hc2, k + 1, nrm2, inv, s, brk)) return -1;
         if (vec_scale_dev(w, nn, inv, s)) return -1;
     }
-    *k_out = m;
+    int kb = 0;
+    LB_CHECK_CUDA(cudaMemcpyAsync(&kb, brk, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LB_CHECK_CUDA(cudaStreamSynchronize(s));
+    *k_out = (kb > 0 && kb < m) ? kb : m;
     return 0;
 }
 
@@ -335,6 +354,9 @@ void lb_default_opts(lb_opts* o) {
     o->keep_ritz = 0;
     o->route = LB_ROUTE_SCHUR;
     o->eig_cond_max = 1e3;
+    o->schur_tol = 1e-12;
+    o->recycle_k = 8;
+    o->gauge_c = nullptr;
 }
 
 const char* lb_status_string(int st) {
@@ -508,6 +530,18 @@ lb_status lindblad_setup(const void* H_dev, const void* L_dev, int n, int d, voi
     h->schur_err = diag[1] / std::max(diag[3], 1e-300);
     h->min_re_T = diag[4];
     h->case1 = h->min_re_T <= 1e3 * 2.220446049250313e-16 * h->gnorm;
+    if (!(h->schur_err <= o.schur_tol)) {
+        // the QR of the eigenvector matrix is not a backward-stable Schur form when the eigenvectors
+        // are ill-conditioned: refuse rather than precondition with the factor of another matrix
+        fprintf(stderr, "lindblad: Schur backward error %.3e above the gate %.3e\n", h->schur_err, o.schur_tol);
+        if (info) {
+            std::memset(info, 0, sizeof(*info));
+            info->schur_backward_err = h->schur_err;
+            info->min_abs_re_T = h->min_re_T;
+            info->status = LB_SOLVER_ERROR;
+        }
+        return fail(LB_SOLVER_ERROR);
+    }
     lb_status ret = LB_OK;
     if (o.route != LB_ROUTE_SCHUR) {
         double nr[4];
@@ -730,6 +764,7 @@ lb_status steady_state_arnoldi(lb_handle_s* h, cudaStream_t s, const lb_opts& o,
                 inf->residual_fro = rfro;
                 LB_CHECK_CUDA(cudaMemcpyAsync(rho_out, rho, nn * sizeof(cplx), cudaMemcpyDeviceToDevice, s));
                 LB_CHECK_CUDA(cudaMemcpyAsync(h->best, rt, nn * sizeof(cplx), cudaMemcpyDeviceToDevice, s));
+                LB_CHECK_CUDA(cudaMemcpyAsync(h->Rres, R, nn * sizeof(cplx), cudaMemcpyDeviceToDevice, s));
             }
             if (rmax < o.tol || prec == LB_PREC_MIXED) { ++restart; break; }
         }

@@ -294,20 +294,24 @@ int pure_state_case1(lb_handle_s* h, cudaStream_t s, cplx* rho_out) {
 // Residual correction of the steady state (mixed precision): r = L(rho) in FP64; solve
 // (0 - L~_eta) delta = r approximately by preconditioned GMRES (Alg. 3's operator, Alg. 2's
 // preconditioner at lambda = 0); rho <- hermitise(rho + delta), trace 1.  rho is the
-// original-basis state (in/out); its Schur-coordinate copy is kept in h->best.
+// original-basis state (in/out); its Schur-coordinate copy is kept in h->best, and h->Rres holds
+// L(rho) of that accepted state on entry (written by the Arnoldi phase), so each step costs one
+// FP64 Lindbladian.  A step that does not lower ||L(rho)||_max is undone and ends the loop, so the
+// returned state is always the best one seen (the running best of Alg. 4).
 lb_status refine_steady_state(lb_handle_s* h, cudaStream_t s, const lb_opts& o, cplx* rho, lb_info* inf) {
     const int n = h->n;
     const long long nn = (long long)n * n;
+    const size_t bytes = (size_t)nn * sizeof(cplx);
     lb_status st = precond_prepare(h, s, 0.0, o.eta, o.precision, 0);
     if (st != LB_OK) return st;
-    cplx* R = h->X[1];
+    cplx* Racc = h->Rres;   // L(rho) of the accepted iterate
+    cplx* Rnew = h->X[1];
     cplx* rt = h->X[2];
     cplx* delta = h->X[3];
-    cplx* rs = h->best;   // Schur-coordinate state
+    cplx* rs = h->best;     // Schur-coordinate state
     double rmax = inf->residual_max, rfro = inf->residual_fro;
     for (int it = 0; it < o.max_refine && rmax >= o.tol; ++it) {
-        if (lindbladian_f64(h, s, rho, R)) return LB_CUDA_ERROR;
-        if (change_basis(h, s, R, rt, h->X[4], 1)) return LB_CUDA_ERROR;
+        if (change_basis(h, s, Racc, rt, h->X[4], 1)) return LB_CUDA_ERROR;
         if (vec_scale_copy(delta, rt, nn, cmake(0, 0), s)) return LB_CUDA_ERROR;
         int steps = 0;
         double res = 0.0;
@@ -315,12 +319,26 @@ lb_status refine_steady_state(lb_handle_s* h, cudaStream_t s, const lb_opts& o, 
             return LB_CUDA_ERROR;
         inf->gmres_steps += steps;
         inf->refine_steps += 1;
+        LB_CHECK_CUDA(cudaMemcpyAsync(h->bk0, rho, bytes, cudaMemcpyDeviceToDevice, s));
+        LB_CHECK_CUDA(cudaMemcpyAsync(h->bk1, rs, bytes, cudaMemcpyDeviceToDevice, s));
         if (vec_axpby(rs, delta, nn, cmake(1, 0), cmake(1, 0), s)) return LB_CUDA_ERROR;
         if (hermitize_normalize(h, s, rs, rs, h->X[4])) return LB_CUDA_ERROR;
         if (change_basis(h, s, rs, rho, h->X[4], 0)) return LB_CUDA_ERROR;
         if (hermitize_normalize(h, s, rho, rho, h->X[4])) return LB_CUDA_ERROR;
-        if (residual_norms(h, s, rho, R, &rmax, &rfro)) return LB_CUDA_ERROR;
+        double nmax = 0.0, nfro = 0.0;
+        if (residual_norms(h, s, rho, Rnew, &nmax, &nfro)) return LB_CUDA_ERROR;
+        if (!(nmax < rmax)) {
+            // no progress (the correction hit the low-precision floor): keep the accepted iterate
+            LB_CHECK_CUDA(cudaMemcpyAsync(rho, h->bk0, bytes, cudaMemcpyDeviceToDevice, s));
+            LB_CHECK_CUDA(cudaMemcpyAsync(rs, h->bk1, bytes, cudaMemcpyDeviceToDevice, s));
+            break;
+        }
+        std::swap(Racc, Rnew);
+        rmax = nmax;
+        rfro = nfro;
     }
+    if (Racc != h->Rres) LB_CHECK_CUDA(cudaMemcpyAsync(h->Rres, Racc, bytes, cudaMemcpyDeviceToDevice, s));
+    LB_CHECK_CUDA(cudaStreamSynchronize(s));
     inf->residual_max = rmax;
     inf->residual_fro = rfro;
     return rmax < o.tol ? LB_OK : LB_NOT_CONVERGED;

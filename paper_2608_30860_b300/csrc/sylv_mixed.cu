@@ -267,13 +267,7 @@ int sylv_mixed_prepare(lb_handle_s* h, char* base, cudaStream_t s) {
     if (tc_make_map(&m->maps.m[1], m->XTp, (int)np, (int)np, 1, (int)np, 1)) return -1;
     if (tc_make_map(&m->maps.m[2], m->Xp, (int)np, (int)np, 1, (int)np, 1)) return -1;
     m->maps.m[3] = m->maps.m[0];
-    static bool attr = false;
-    if (!attr) {
-        if (cudaFuncSetAttribute(k_sylv_leaf128, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LEAF_SMEM) !=
-            cudaSuccess)
-            return -1;
-        attr = true;
-    }
+    if (lb_smem_attr((const void*)k_sylv_leaf128, (int)LEAF_SMEM)) return -1;
     h->mixed_sylv_ready = true;
     return 0;
 }

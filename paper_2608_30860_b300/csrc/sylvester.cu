@@ -158,11 +158,7 @@ trisylv_f64_wave(const cplx* __restrict__ T, cplx* __restrict__ X, int n, cplx s
 int trisylv_f64(const cplx* T, cplx* X, int n, cplx s, cudaStream_t st) {
     const int nb = (n + SB - 1) / SB;
     const size_t smem = 3 * SB * (SB + 1) * sizeof(cplx);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(trisylv_f64_wave, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr_set = true;
-    }
+    if (lb_smem_attr((const void*)trisylv_f64_wave, (int)smem)) return -1;
     for (int w = 0; w <= 2 * nb - 2; ++w) {
         int lo = w - (nb - 1) > 0 ? w - (nb - 1) : 0;
         int hi = w < nb - 1 ? w : nb - 1;

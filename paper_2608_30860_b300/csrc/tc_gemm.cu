@@ -462,13 +462,7 @@ int tc_make_map(CUtensorMap* map, const void* planes, int K, int rows, int nbatc
 }
 
 int tc_gemm_launch(const tc::Maps& maps, const tc::Params& p, int grid_m, int grid_n, cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
-        if (cudaFuncSetAttribute(tc::k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES) !=
-            cudaSuccess)
-            return -1;
-        attr = true;
-    }
+    if (lb_smem_attr((const void*)tc::k_tc_gemm, tc::SMEM_BYTES)) return -1;
     if (grid_m <= 0 || grid_n <= 0 || p.nseg < 1 || p.nseg > tc::MAX_SEGS) return -1;
     if (p.wave < 0)
         for (int g = 0; g < p.nseg; ++g)

@@ -82,12 +82,25 @@ __global__ void __launch_bounds__(RT) k_gemv(cplx* __restrict__ y, const cplx* _
 
 // Arnoldi column finalisation: hcol[i] += h2[i]; beta = ||w|| (from |w|^2 in nrm2);
 // hcol[k] = beta; inv[0] = 1/beta.
-__global__ void k_finish_column(cplx* hcol, const cplx* h2, int k, const cplx* nrm2, cplx* inv) {
+// Completes Hessenberg column k-1 (k entries from the two Gram-Schmidt passes, then the norm) and
+// the scale 1/h_{k,k-1} of the next basis vector.  With brk non-null, breakdown is detected here:
+// h_{k,k-1} <= 1e-13 max(1, max_i |h_{i,k-1}|) records k in brk[0] (if still 0) and sets the scale
+// to 0, so that the remaining steps of the cycle carry zero vectors and the host reads the step
+// count once per cycle instead of once per step.
+__global__ void k_finish_column(cplx* hcol, const cplx* h2, int k, const cplx* nrm2, cplx* inv, int* brk) {
     for (int i = threadIdx.x; i < k; i += blockDim.x) hcol[i] = cadd(hcol[i], h2[i]);
+    __syncthreads();
     if (threadIdx.x == 0) {
         double b = sqrt(fmax(nrm2[0].x, 0.0));
+        double hmax = 0.0;
+        for (int i = 0; i < k; ++i) hmax = fmax(hmax, hypot(hcol[i].x, hcol[i].y));
+        bool dead = !(b > 0.0);
+        if (brk) {
+            dead = dead || brk[0] != 0 || !(b > 1e-13 * fmax(1.0, hmax));
+            if (dead && brk[0] == 0) brk[0] = k;
+        }
         hcol[k] = cmake(b, 0.0);
-        inv[0] = cmake(b > 0.0 ? 1.0 / b : 0.0, 0.0);
+        inv[0] = cmake(dead ? 0.0 : 1.0 / b, 0.0);
     }
 }
 
@@ -282,8 +295,8 @@ int vec_gemv(cplx* y, const cplx* V, long long vstride, int k, const cplx* h, lo
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int vec_finish_column(cplx* hcol, const cplx* h2, int k, const cplx* nrm2, cplx* inv, cudaStream_t s) {
-    k_finish_column<<<1, 128, 0, s>>>(hcol, h2, k, nrm2, inv); lb_note_launch();
+int vec_finish_column(cplx* hcol, const cplx* h2, int k, const cplx* nrm2, cplx* inv, cudaStream_t s, int* brk) {
+    k_finish_column<<<1, 128, 0, s>>>(hcol, h2, k, nrm2, inv, brk); lb_note_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

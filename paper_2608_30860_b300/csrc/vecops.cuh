@@ -10,7 +10,10 @@ int vec_dot_block(const cplx* V, long long vstride, int k, const cplx* w, long l
 // y = (keep_y ? y : 0) + sign * sum_i h[i] V_i   (k <= 128)
 int vec_gemv(cplx* y, const cplx* V, long long vstride, int k, const cplx* h, long long len, double sign,
              int keep_y, cudaStream_t s);
-int vec_finish_column(cplx* hcol, const cplx* h2, int k, const cplx* nrm2, cplx* inv, cudaStream_t s);
+// hcol[0..k) += h2; hcol[k] = sqrt(nrm2); inv = 1 / hcol[k] (0 on breakdown, recorded in brk[0] = k
+// when brk is non-null and still 0)
+int vec_finish_column(cplx* hcol, const cplx* h2, int k, const cplx* nrm2, cplx* inv, cudaStream_t s,
+                      int* brk = nullptr);
 int vec_scale_dev(cplx* x, long long len, const cplx* a, cudaStream_t s);
 int vec_scale_copy(cplx* y, const cplx* x, long long len, cplx a, cudaStream_t s);
 int vec_axpby(cplx* y, const cplx* x, long long len, cplx a, cplx b, cudaStream_t s);

@@ -39,7 +39,9 @@ class LbOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("krylov_m", ctypes.c_int), ("max_restarts", ctypes.c_int),
                 ("precision", ctypes.c_int), ("eta", ctypes.c_double), ("max_refine", ctypes.c_int),
                 ("gmres_m", ctypes.c_int), ("sylv_block", ctypes.c_int), ("inner_tol", ctypes.c_double),
-                ("keep_ritz", ctypes.c_int), ("route", ctypes.c_int), ("eig_cond_max", ctypes.c_double)]
+                ("keep_ritz", ctypes.c_int), ("route", ctypes.c_int), ("eig_cond_max", ctypes.c_double),
+                ("schur_tol", ctypes.c_double), ("recycle_k", ctypes.c_int),
+                ("gauge_c", ctypes.POINTER(ctypes.c_double))]
 
 
 class LbInfo(ctypes.Structure):

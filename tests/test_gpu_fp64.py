@@ -240,3 +240,18 @@ def test_eigenbasis_route_gate_refuses(B):
     ref = D.unvec(D.Phi_super(H, Ls) @ D.vec(X), 40)
     assert _rel(B.phi_apply(h, _cuda(X)).cpu().numpy(), ref) < 1e-11
     B.lindblad_destroy(h)
+
+
+def test_schur_backward_error_gate(B):
+    """The set-up's Schur form (QR of the eigenvector matrix) on a non-normal Kerr cat (n = 160,
+    eps2 = 8: eigenvector condition ~35) stays backward stable, ||lower(Q^dag G Q)||_F / ||G||_F
+    below the default gate; a gate below that value makes the set-up fail with LB_SOLVER_ERROR
+    instead of returning the Schur factor of another matrix."""
+    H, Ls = gi.kerr_cat(160, eps2=8.0)
+    h, _ = _setup(B, H, Ls)
+    err = h.setup_info["schur_backward_err"]
+    assert 0.0 < err < 1e-12
+    B.lindblad_destroy(h)
+    with pytest.raises(B.LindbladError) as e:
+        _setup(B, H, Ls, schur_tol=0.1 * err)
+    assert e.value.status == -6

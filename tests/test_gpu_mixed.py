@@ -119,3 +119,18 @@ def test_mixed_steady_state_refined_to_fp64(B, name, make):
         bar = max(bar, 10 * info["residual_fro"] / sigma2 / np.linalg.norm(ref))
     assert np.linalg.norm(rho - ref) / np.linalg.norm(ref) < bar
     B.lindblad_destroy(h)
+
+
+def test_refinement_cap_returns_the_running_best(B):
+    """max_refine = 1 with an unreachable tolerance: LB_NOT_CONVERGED (1), and the state returned is
+    the best one seen, with the residual the library reports equal to the one recomputed from it."""
+    H, Ls = gi.random_lindbladian(96, d=3, seed=2)
+    h = B.lindblad_setup(_cuda(H), _cuda(np.stack(Ls)))
+    opts = B.default_opts(precision=B.LB_PREC_MIXED, tol=1e-30, max_refine=1)
+    rho, info, st = B.steady_state(h, opts)
+    assert st == 1 and info["refine_steps"] == 1
+    R = B.lindbladian_apply(h, rho)
+    assert abs(float(R.abs().max()) - info["residual_max"]) <= 1e-3 * info["residual_max"]
+    # one refinement step from the low-precision Arnoldi state already lands well below its residual
+    assert info["residual_max"] < 1e-9
+    B.lindblad_destroy(h)
