@@ -180,9 +180,49 @@ lb_status lindbladian_apply(lindblad_handle h, const void* X_dev, void* R_dev, v
 lb_status steady_state(lindblad_handle h, void* rho_dev, const lb_opts* opts, lb_info* info,
                        void* stream);
 
+/* Steady state as a preconditioned linear solve (Alg. 3, Sec. 4.1): L~_eta rho = eta I with
+ * L~_eta(rho) = L(rho) + eta Tr(rho) I (Eq. steady_state_linear_problem), by GMRES right-preconditioned
+ * with P_0 = Precond(., 0, eta) (Alg. 2, Eq. ShermanMorr) and Krylov subspace recycling (App. A.2:
+ * opts->recycle_k harmonic Ritz vectors kept across restarts), warm start |0><0|.  After every
+ * GMRES cycle (FP64) the iterate is hermitised and trace-normalised and the solve stops when
+ * ||L(rho_hat)||_max < opts->tol.  With LB_PREC_MIXED the GMRES cycles run on the tensor cores and
+ * each correction is checked against the FP64 residual (residual-correction refinement).
+ *   rho_dev : n x n device output (Hermitian, trace 1): the best iterate.
+ * Cycle length opts->gmres_m; at most opts->max_restarts corrections (FP64) or opts->max_refine + 4
+ * (mixed).  info: restarts = GMRES cycles, gmres_steps = phi_applies = preconditioned operator
+ * applications (one Lyapunov solve + one jump term each), refine_steps = FP64 residual corrections.
+ * Returns LB_OK, LB_NOT_CONVERGED (best state returned), LB_S_SINGULAR (case 1 of Theorem 1: S not
+ * invertible, no result), LB_ETA_EXCLUDED, LB_INVALID_ARG, LB_CUDA_ERROR. */
+lb_status steady_state_gmres(lindblad_handle h, void* rho_dev, const lb_opts* opts, lb_info* info, void* stream);
+
+/* Resolvent of the Lindbladian (Corollary "Resolvent of the Lindbladian"; the benchmark of Sec. 3.4):
+ * X = R_lam^L(B) = (lam - L)^{-1}(B) for lam > 0, by recycled GMRES right-preconditioned with the
+ * no-jump resolvent R_lam^S ((lam - L) R_lam^S = Id - K R_lam^S, Theorem 2: a strict contraction, so
+ * the inner solve converges geometrically).  The iterate is hermitised when B is Hermitian and
+ * rescaled to its exact trace Tr B / lam; the solve stops when ||(lam - L)(X) - B||_max < opts->tol.
+ *   B_dev, X_dev : n x n device complex128 (must not alias).  X is written (no warm start).
+ * The recycled subspace is kept in the handle for later solves at the same lam and precision.
+ * Returns LB_OK, LB_NOT_CONVERGED (last iterate returned), LB_INVALID_ARG (lam <= 0, null or aliased
+ * pointers), LB_NOT_IMPLEMENTED, LB_CUDA_ERROR. */
+lb_status resolvent_solve(lindblad_handle h, double lam, const void* B_dev, void* X_dev, const lb_opts* opts,
+                          lb_info* info, void* stream);
+
+/* Implicit Euler time stepping (Eq. resolvent, Sec. 4.3): rho_{k+1} = (Id - dt L)^{-1} rho_k
+ * = (1/dt) R_{1/dt}^L rho_k for nsteps steps, each a resolvent solve at lam = 1/dt preconditioned by
+ * R_{1/dt}^S (Theorem 2 applies: lam > 0), warm-started from rho_k, with the recycled subspace carried
+ * from step to step.  A step stops when ||(1/dt - L)(rho_{k+1}) - rho_k / dt||_max < opts->tol
+ * ||rho_k / dt||_max (rho_{k+1} hermitised for Hermitian rho0, trace = Tr rho_k).
+ *   rho0_dev : n x n device initial state; rho_dev : n x n device final state (must differ);
+ *   traj_dev : nullable, nsteps stacked n x n device states after each step.
+ * info: residual_max = the largest relative step residual, gmres_steps / phi_applies / restarts summed.
+ * Returns LB_OK, LB_NOT_CONVERGED (a step missed the tolerance; the trajectory continues),
+ * LB_INVALID_ARG (dt <= 0, nsteps < 1), LB_NOT_IMPLEMENTED, LB_CUDA_ERROR. */
+lb_status implicit_euler(lindblad_handle h, const void* rho0_dev, double dt, int nsteps, void* rho_dev,
+                         void* traj_dev, const lb_opts* opts, lb_info* info, void* stream);
+
 /* The k smallest-|lambda| nonzero eigenvalues of L by shift-invert Arnoldi on
  * (mu - L~_eta)^{-1} (Alg. 5), each application a GMRES solve right-preconditioned by
- * Precond(., mu, eta) (Alg. 2).  Thick (Krylov-Schur) restarts keep opts->keep_ritz pairs;
+ * Precond(., mu, eta) (Alg. 2), recycled across cycles and across applications (App. A.2).  Thick (Krylov-Schur) restarts keep opts->keep_ritz pairs;
  * stop when max_k ||L v_k - lambda_k v_k||_max / ||v_k||_max < opts->tol.
  *   evals_host : k complex128 (host memory), sorted by |lambda|, then Re descending.
  *   evecs_dev  : nullable; k stacked n x n device eigenvectors (raw, traceless).

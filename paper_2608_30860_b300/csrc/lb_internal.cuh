@@ -33,6 +33,14 @@ struct lb_handle_s {
     cplx* P = nullptr;                 // d n^2 scratch (jump-term intermediate)
     cplx* X[NSCRATCH] = {};            // n x n scratch
     cplx* best = nullptr;              // n x n
+    // recycled GMRES (recycle.cu): pair (U^, C) with B U^ = C diag(dU), U^ unit columns, C orthonormal
+    int rk = 0;                        // capacity (vectors)
+    cplx *Urc = nullptr, *Crc = nullptr, *Unw = nullptr, *Cnw = nullptr;
+    double* dU = nullptr;              // 2 x 16: current and next scale factors
+    cplx* gsm = nullptr;               // small dense matrices of the GCRO-DR cycle
+    int rc_have = 0;                   // size of the pair in use (0: none)
+    double rc_mu = 0.0, rc_eta = 0.0;  // operator the pair belongs to
+    int rc_prec = -1;
     cplx* Rres = nullptr;              // L(rho) of the accepted steady-state iterate (original basis)
     cplx* bk0 = nullptr;               // backups of the accepted iterate during refinement
     cplx* bk1 = nullptr;
@@ -44,6 +52,8 @@ struct lb_handle_s {
     cplx* E1 = nullptr;                // eigenbasis-route scratch (n x n each)
     cplx* E2 = nullptr;
     bool eig_active = false;           // FP64 Lyapunov solves use the eigenbasis route
+    int arn_depth = 0;                 // nesting level of arnoldi_cycle (breakdown flag dinfo[12 + level])
+    bool gauged = false;               // H, L hold the gauge-shifted H~, L~_j (lb_opts.gauge_c)
     double cond_eig = 0.0;
     bool ua_ready = false;
     cplx* V = nullptr;                 // inner Krylov basis (vcap vectors)
@@ -99,12 +109,22 @@ lb_status check_device_error(lb_handle_s* h, cudaStream_t s);
 lb_status steady_state_arnoldi(lb_handle_s* h, cudaStream_t s, const lb_opts& o, cplx* rho_out, lb_info* inf);
 
 // solvers.cu
+lb_status precond_prepare(lb_handle_s* h, cudaStream_t s, double mu, double eta, int precision, int adj);
+int precond_apply(lb_handle_s* h, cudaStream_t s, const cplx* X, cplx* out, double mu, double eta, int precision,
+                  int adj);
 int pure_state_case1(lb_handle_s* h, cudaStream_t s, cplx* rho_out);
 lb_status refine_steady_state(lb_handle_s* h, cudaStream_t s, const lb_opts& o, cplx* rho, lb_info* inf);
 
 lb_status adj_precond_prepare(lb_handle_s* h, cudaStream_t s, double eta);
 int adj_gmres_solve(lb_handle_s* h, cudaStream_t s, const cplx* b, cplx* x, double eta, int m, int max_cycles,
                     double atol, int* steps, double* final_res);
+
+// recycle.cu
+size_t recycle_bytes(int n, int rk);
+void recycle_layout(lb_handle_s* h, char*& base, int rk);
+void recycle_forget(lb_handle_s* h);
+int gcrodr_solve(lb_handle_s* h, cudaStream_t s, const cplx* b, cplx* delta, double mu, double eta, int m, int kreq,
+                 int max_cycles, double atol, int precision, int* steps, double* final_res, int* cycles_out);
 
 // adjoint.cu
 int adj_lyap_schur(lb_handle_s* h, cudaStream_t s, const cplx* Y, cplx* X, double shift);

@@ -42,6 +42,13 @@ int krylov_cap(const lb_opts* o) {
     return std::max(std::max(m, g), 4);
 }
 
+// recycled-GMRES capacity: opts->recycle_k clipped to [0, 16] and to gmres_m - 2
+int recycle_cap(const lb_opts* o) {
+    int k = o ? o->recycle_k : 8;
+    int g = o ? o->gmres_m : 40;
+    return std::max(0, std::min(std::min(k, 16), g - 2));
+}
+
 size_t cusolver_ws_bytes(int n, size_t* host_bytes) {
     cusolverDnHandle_t hs = nullptr;
     cusolverDnParams_t prm = nullptr;
@@ -107,6 +114,13 @@ void layout(lb_handle_s* h, char* base, int n, int d, const lb_opts* o, size_t s
     h->solver_ws = c.take<char>(solver_ws);
     h->solver_ws_bytes = solver_ws;
     h->mixed_base = c.take<char>(mixed_bytes(n, d));
+    {
+        const int rk = recycle_cap(o);
+        h->n = n;
+        char* rb = c.take<char>(recycle_bytes(n, rk));
+        if (base) recycle_layout(h, rb, rk);
+        h->rk = rk;
+    }
     h->ws_bytes = c.off + 256;
 }
 
@@ -259,7 +273,14 @@ int arnoldi_cycle(lb_handle_s* h, cudaStream_t s, cplx* basis, cplx* hess, int j
     cplx* hc2 = h->small;
     cplx* nrm2 = h->small + (KMAX + 2);
     cplx* inv = h->small + 2 * (KMAX + 2);
-    int* brk = h->dinfo + 12;
+    // one flag per nesting level: the shift-invert Arnoldi runs an inner GMRES cycle inside each step
+    if (h->arn_depth >= 4) return -1;
+    int* brk = h->dinfo + 12 + h->arn_depth;
+    struct Depth {
+        int& d;
+        explicit Depth(int& v) : d(v) { ++d; }
+        ~Depth() { --d; }
+    } depth_guard(h->arn_depth);
     LB_CHECK_CUDA(cudaMemsetAsync(brk, 0, sizeof(int), s));
     for (int k = j0; k < m; ++k) {
         cplx* w = basis + (k + 1) * nn;
@@ -414,6 +435,13 @@ lb_status lindblad_setup(const void* H_dev, const void* L_dev, int n, int d, voi
     if (cudaMemcpyAsync(h->H, H_dev, nn * sizeof(cplx), cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(h->L, L_dev, (size_t)d * nn * sizeof(cplx), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return fail(LB_CUDA_ERROR);
+    if (o.gauge_c) {
+        // gauge of the split: the handle then holds (H~, L~_j); L is unchanged, S~ and K~ are not
+        if (cudaMemcpyAsync(h->part, o.gauge_c, (size_t)d * sizeof(cplx), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            gauge_split(h->H, h->L, n, d, h->part, s))
+            return fail(LB_CUDA_ERROR);
+        h->gauged = true;
+    }
     // G = -iH - 1/2 sum_j L_j^dag L_j  (one stacked GEMM, K = d n)
     if (vec_scale_copy(h->G, h->H, nn, cmake(0, -1), s)) return fail(LB_CUDA_ERROR);
     {

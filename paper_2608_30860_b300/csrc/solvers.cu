@@ -162,7 +162,7 @@ double read_double(cudaStream_t s, const double* d) {
 // ============================================================================ Alg. 2
 // W = R_mu^S(I) in Schur coordinates and its trace (scal[8]); returns LB_ETA_EXCLUDED if
 // |1 - eta Tr W| is negligible (Eq. ShermanMorr).
-static lb_status precond_prepare(lb_handle_s* h, cudaStream_t s, double mu, double eta, int precision, int adj) {
+lb_status precond_prepare(lb_handle_s* h, cudaStream_t s, double mu, double eta, int precision, int adj) {
     const int n = h->n;
     cplx* W = adj ? h->Wa : h->W;
     // (mu - S~) W = I  <=>  T_mu W + W T_mu^dag = -I   (adjoint: T_mu^dag W + W T_mu = -I)
@@ -178,20 +178,23 @@ static lb_status precond_prepare(lb_handle_s* h, cudaStream_t s, double mu, doub
     return LB_OK;
 }
 
-// out = Precond(X, mu, eta) = Z + eta Tr Z / (1 - eta Tr W) W, Z = R_mu^S(X)  (Alg. 2)
-static int precond_apply(lb_handle_s* h, cudaStream_t s, const cplx* X, cplx* out, double mu, double eta,
-                         int precision, int adj) {
+// out = Precond(X, mu, eta) = Z + eta Tr Z / (1 - eta Tr W) W, Z = R_mu^S(X)  (Alg. 2); with eta = 0
+// it is the plain no-jump resolvent R_mu^S (the preconditioner of the undeflated systems) and W is
+// not read
+int precond_apply(lb_handle_s* h, cudaStream_t s, const cplx* X, cplx* out, double mu, double eta, int precision,
+                  int adj) {
     const long long nn = (long long)h->n * h->n;
     if (vec_scale_copy(out, X, nn, cmake(-1, 0), s)) return -1;                // -X
     if (adj ? adj_lyap_schur(h, s, out, out, 0.5 * mu) : lyap_schur(h, s, out, out, 0.5 * mu, precision))
         return -1;                                                               // Z
+    if (eta == 0.0) return 0;
     if (mat_trace(out, h->n, h->scal + 9, s)) return -1;
     k_sm_combine<<<grid1(nn), 256, 0, s>>>(out, adj ? h->Wa : h->W, nn, h->scal + 9, h->scal + 8, eta); lb_note_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 // out = (mu - L~_eta)(X) = mu X - (T X + X T^dag) - K~(X) - eta Tr(X) I   (Schur coordinates)
-static int shifted_deflated_apply(lb_handle_s* h, cudaStream_t s, const cplx* X, cplx* out, double mu, double eta,
+[[maybe_unused]] static int shifted_deflated_apply(lb_handle_s* h, cudaStream_t s, const cplx* X, cplx* out, double mu, double eta,
                                   int precision) {
     const int n = h->n;
     const long long nn = (long long)n * n;
@@ -397,7 +400,8 @@ extern "C" lb_status low_spectrum(lindblad_handle h, int k, double mu, double et
         bn = read_double(s, h->dscal + 1);
         int steps = 0;
         double res = 0.0;
-        if (gmres_solve(h, s, b, xsol, mu, eta, o.gmres_m, 50, o.inner_tol * bn, o.precision, &steps, &res))
+        if (gcrodr_solve(h, s, b, xsol, mu, eta, o.gmres_m, o.recycle_k, 50, o.inner_tol * bn, o.precision, &steps,
+                         &res, nullptr))
             return -1;
         inf.gmres_steps += steps;
         inf.phi_applies += 1;

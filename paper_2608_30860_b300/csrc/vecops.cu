@@ -336,6 +336,37 @@ int vec_norms(const cplx* x, long long len, double* part, double* out, cudaStrea
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
+// Gauge of the no-jump / jump split (Remark "Non-uniqueness of the decomposition"):
+// (1) L~_k = L_k + c_k I in place; (2) H~ = H + (1/2i) sum_k (conj(c_k) L~_k - c_k L~_k^dag) in place.
+__global__ void k_gauge_jumps(cplx* L, int n, int d, const cplx* c) {
+    const long long nn = (long long)n * n;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)d * n; e += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(e / n), i = (int)(e % n);
+        cplx* p = L + k * nn + (long long)i * n + i;
+        *p = cadd(*p, c[k]);
+    }
+}
+__global__ void k_gauge_hamiltonian(cplx* H, const cplx* Lt, int n, int d, const cplx* c) {
+    const long long nn = (long long)n * n;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nn; e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / n), j = (int)(e % n);
+        cplx acc = cmake(0, 0);
+        for (int k = 0; k < d; ++k) {
+            const cplx a = Lt[k * nn + e];                           // L~_k[i][j]
+            const cplx bdag = cconj(Lt[k * nn + (long long)j * n + i]);   // (L~_k^dag)[i][j]
+            acc = cadd(acc, csub(cmul(cconj(c[k]), a), cmul(c[k], bdag)));
+        }
+        // (1/2i) acc = -i acc / 2
+        H[e] = cadd(H[e], cmake(0.5 * acc.y, -0.5 * acc.x));
+    }
+}
+
+int gauge_split(cplx* H, cplx* L, int n, int d, const cplx* c_dev, cudaStream_t s) {
+    k_gauge_jumps<<<grid_for((long long)d * n), RT, 0, s>>>(L, n, d, c_dev); lb_note_launch();
+    k_gauge_hamiltonian<<<grid_for((long long)n * n), RT, 0, s>>>(H, L, n, d, c_dev); lb_note_launch();
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 int mat_eye(cplx* X, int n, cplx a, cudaStream_t s) {
     k_eye<<<grid_for((long long)n * n), RT, 0, s>>>(X, n, a); lb_note_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : -1;

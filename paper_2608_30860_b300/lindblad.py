@@ -85,6 +85,12 @@ def load_library(path: str = LIB_PATH):
     lib.lindbladian_apply.restype = i
     lib.steady_state.argtypes = [vp, vp, P(LbOpts), P(LbInfo), vp]
     lib.steady_state.restype = i
+    lib.steady_state_gmres.argtypes = [vp, vp, P(LbOpts), P(LbInfo), vp]
+    lib.steady_state_gmres.restype = i
+    lib.resolvent_solve.argtypes = [vp, d, vp, vp, P(LbOpts), P(LbInfo), vp]
+    lib.resolvent_solve.restype = i
+    lib.implicit_euler.argtypes = [vp, vp, d, i, vp, vp, P(LbOpts), P(LbInfo), vp]
+    lib.implicit_euler.restype = i
     lib.low_spectrum.argtypes = [vp, i, d, d, vp, vp, P(LbOpts), P(LbInfo), vp]
     lib.low_spectrum.restype = i
     lib.steady_state_adjoint.argtypes = [vp, vp, vp, vp, vp, vp, P(LbOpts), P(LbInfo), vp]
@@ -212,6 +218,46 @@ def steady_state(h: Handle, opts: LbOpts | None = None, rho: torch.Tensor | None
     if st < 0:
         raise LindbladError(st, "steady_state")
     return rho, info.as_dict(), st
+
+
+def steady_state_gmres(h: Handle, opts: LbOpts | None = None, rho: torch.Tensor | None = None):
+    """Alg. 3 (recycled preconditioned GMRES).  Returns (rho, info dict, status); raises on negative status."""
+    o = opts or default_opts()
+    rho = torch.empty((h.n, h.n), dtype=torch.complex128, device=h.workspace.device) if rho is None else rho
+    info = LbInfo()
+    st = load_library().steady_state_gmres(h.ptr, _dev(rho, (h.n, h.n)), ctypes.byref(o), ctypes.byref(info),
+                                           _stream())
+    if st < 0 or st == 2:
+        raise LindbladError(st, "steady_state_gmres")
+    return rho, info.as_dict(), st
+
+
+def resolvent_solve(h: Handle, lam: float, B: torch.Tensor, opts: LbOpts | None = None,
+                    X: torch.Tensor | None = None):
+    """X = (lam - L)^{-1}(B), lam > 0.  Returns (X, info dict, status); raises on negative status."""
+    o = opts or default_opts()
+    X = torch.empty_like(B) if X is None else X
+    info = LbInfo()
+    st = load_library().resolvent_solve(h.ptr, float(lam), _dev(B, (h.n, h.n)), _dev(X, (h.n, h.n)),
+                                        ctypes.byref(o), ctypes.byref(info), _stream())
+    if st < 0:
+        raise LindbladError(st, "resolvent_solve")
+    return X, info.as_dict(), st
+
+
+def implicit_euler(h: Handle, rho0: torch.Tensor, dt: float, nsteps: int, opts: LbOpts | None = None,
+                   trajectory: bool = False):
+    """nsteps implicit Euler steps from rho0.  Returns (rho, trajectory (nsteps, n, n) or None, info, status)."""
+    o = opts or default_opts()
+    rho = torch.empty_like(rho0)
+    traj = torch.empty((nsteps, h.n, h.n), dtype=torch.complex128, device=rho0.device) if trajectory else None
+    info = LbInfo()
+    st = load_library().implicit_euler(h.ptr, _dev(rho0, (h.n, h.n)), float(dt), int(nsteps), _dev(rho),
+                                       None if traj is None else traj.data_ptr(), ctypes.byref(o),
+                                       ctypes.byref(info), _stream())
+    if st < 0:
+        raise LindbladError(st, "implicit_euler")
+    return rho, traj, info.as_dict(), st
 
 
 def low_spectrum(h: Handle, k: int, mu: float = 0.0, eta: float = 1.0, want_vectors: bool = False,
