@@ -278,7 +278,9 @@ def gcrodr(matvec, precond, b, x0, m=32, k=8, recycle=None, atol=0.0, max_cycles
     m - k steps, giving B [U D, V_p] = [C, V_{p+1}] G with G = [[D, C^H B V_p], [0, Hbar]]
     (D scales U to unit columns); y minimises ||[C, V_{p+1}]^H r - G y||.  After each cycle the
     k harmonic Ritz vectors of B on range([U D, V_p]) with the smallest harmonic Ritz values,
-    i.e. G^H G z = theta G^H [C, V_{p+1}]^H [U D, V_p] z, become the new (U, C) (QR of G Z).
+    i.e. G^H G z = theta G^H [C, V_{p+1}]^H [U D, V_p] z, become the new (U, C) through the small QR
+    G Z = Q R (C = [C, V_{p+1}] Q, U = [U D, V_p] Z R^{-1}); the problem is posed on an orthonormal basis
+    of range([U D, V_p]) and the pair is kept when R is numerically singular.
     ``recycle`` = (U, C) of an earlier solve with the same operator (kept as is); the returned
     pair is to be passed to the next solve.  ``cycle_hook(x)`` returning True stops early."""
     x = np.array(x0, dtype=np.complex128)
@@ -336,24 +338,40 @@ def gcrodr(matvec, precond, b, x0, m=32, k=8, recycle=None, atol=0.0, max_cycles
         x = x + precond(_combine(What, y))
         r = _combine(Vhat, rhs - G @ y)
         cycles += 1
-        # new recycled pair from the harmonic Ritz vectors of smallest |theta|
+        # new recycled pair: the harmonic Ritz vectors of smallest |theta|, taken on an orthonormal
+        # basis [U D, V_p] S of range([U D, V_p]) (S from the eigenpairs of its Gram matrix above 1e-10 of
+        # the largest: once a cycle has nearly converged [U D, V_p] is numerically rank-deficient and its
+        # null directions would pass for spurious harmonic Ritz vectors), as the Schur vectors of the
+        # selected values; then the small QR G Z = Q R gives C = [C, V_{p+1}] Q, U = [U D, V_p] Z R^{-1}
         F = np.zeros((kk + p + 1, kk + p), dtype=np.complex128)
+        Gam = np.eye(kk + p, dtype=np.complex128)
         for j in range(kk):
             for i in range(kk):
                 F[i, j] = hs_inner(C[i], Ut[j])
+                Gam[i, j] = hs_inner(Ut[i], Ut[j])
             for i in range(p + 1):
                 F[kk + i, j] = hs_inner(V[i], Ut[j])
+            for i in range(p):
+                Gam[kk + i, j] = F[kk + i, j]
+                Gam[j, kk + i] = np.conj(F[kk + i, j])
         F[kk:, kk:] = np.eye(p + 1, p)
-        theta, Z = sla.eig(G.conj().T @ G, G.conj().T @ F)
-        mag = np.where(np.isfinite(theta), np.abs(theta), np.inf)
-        keep = np.argsort(mag)[: min(k, kk + p)]
-        Z = Z[:, keep]
-        Y = [_combine(What, Z[:, t]) for t in range(Z.shape[1])]
-        GZ = G @ Z
-        Ct = [_combine(Vhat, GZ[:, t]) for t in range(Z.shape[1])]
-        C, R = _gs_qr(Ct)
-        Ri = np.linalg.inv(R)
-        U = [_combine(Y, Ri[:, t]) for t in range(len(Y))]
+        lam, E = np.linalg.eigh(Gam)
+        keepg = lam > 1e-10 * lam.max()
+        S = E[:, keepg] / np.sqrt(lam[keepg])
+        GS = G @ S
+        Qg, Rg = np.linalg.qr(GS)
+        Mh = np.linalg.solve(Rg, Qg.conj().T @ (F @ S))      # eigenvalues 1 / theta
+        kq = min(k, Mh.shape[0])
+        mu = np.linalg.eigvals(Mh)
+        thr = np.sort(np.abs(mu))[-kq] * (1.0 - 1e-12)
+        _, Ys, sdim = sla.schur(Mh, output="complex", sort=lambda z: abs(z) >= thr)
+        Z = S @ Ys[:, :min(sdim, kq)]
+        Qs, Rs = np.linalg.qr(G @ Z)
+        dg = np.abs(np.diag(Rs))
+        if dg.size and dg.min() > 1e-12 * dg.max():
+            ZR = Z @ np.linalg.inv(Rs)
+            C = [_combine(Vhat, Qs[:, t]) for t in range(Qs.shape[1])]
+            U = [_combine(What, ZR[:, t]) for t in range(ZR.shape[1])]
         if cycle_hook is not None and cycle_hook(x):
             break
     return x, (U, C), dict(cycles=cycles, steps=steps, residual=hs_norm(r))

@@ -536,13 +536,16 @@ def test_tierb_resolvent_gmres_matches_dense_at_three_shifts():
         rec = None   # each shift is another operator
 
 
-def test_tierb_implicit_euler_gmres_matches_dense():
-    H, Ls = gi.stiff_random_lindbladian(8, K=2.0, seed=1)
-    rho0 = np.zeros((8, 8), dtype=np.complex128)
+@pytest.mark.parametrize("n,m,k", [(8, 12, 4), (16, 40, 8)])
+def test_tierb_implicit_euler_gmres_matches_dense(n, m, k):
+    """Each step's solve converges inside one cycle (lam = 1/dt is large), so the recycled pair is carried
+    across solves from nearly converged cycles: the case that makes [U, V] numerically rank-deficient."""
+    H, Ls = gi.stiff_random_lindbladian(n, K=2.0, seed=1)
+    rho0 = np.zeros((n, n), dtype=np.complex128)
     rho0[0, 0] = 1.0
     dt = 0.05
     ref = D.implicit_euler(H, Ls, rho0, dt, 6)
-    got = K.implicit_euler_gmres(K.System(H, Ls), rho0, dt, 6, tol=1e-12, m=12, k_recycle=4)
+    got = K.implicit_euler_gmres(K.System(H, Ls), rho0, dt, 6, tol=1e-12, m=m, k_recycle=k)
     for a, b in zip(got, ref):
         assert np.abs(a - b).max() < 1e-10
 
