@@ -6,8 +6,14 @@ coordinates (the map Alg. 4 iterates), mixed precision: triangular Lyapunov solv
 term as two tcgen05 split-FP16 GEMMs.  Inputs are synthetic (seeded), already resident in HBM;
 the operands (L~ planes, 1.6 GB) exceed the 126 MB L2, so no flush is needed between steps.
 
-python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--solve]
-python bench.py --workload sweep   # the batched sweep: 1024 Kerr-cat steady states of uneven n
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--quick] [--no-fp64-solve]
+    the default line also carries the set-up time, one FP64 application and the steady-state solve to
+    ||L rho||_max <= 1e-10 in mixed precision and in FP64 (time, residual, iteration counts)
+python bench.py --workload sweep      # the batched sweep: 1024 Kerr-cat steady states of uneven n
+python bench.py --workload resolvent  # (lam - L) X = I/n, three shifts (Sec. 3.4)
+python bench.py --workload euler      # implicit Euler on the stiff n = 32 family (Sec. 4.3)
+python bench.py --workload gmres      # Alg. 3 steady state at n = 4096
+python bench.py --workload cat        # memory-buffer cat: steady state + 3 slowest modes across n
 Multi-GPU: replicas only (each rank runs its own copy of the workload; weak scaling).
 """
 from __future__ import annotations
@@ -110,10 +116,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(n_sites=12, d_sample=1):
+def cpu_baseline(n_sites=12, d_sample=1, repeats=1):
     """The oracle (oracle/krylov.py, NumPy/SciPy FP64) on a bounded sample of one Phi application:
-    the jump term for d_sample of the 12 jump operators at n = 4096 (scaled by 12/d_sample) plus
-    the Bartels-Stewart solve S^{-1} measured at n = 1024 (the 10-site chain, scaled by 4^3)."""
+    the jump term for d_sample of the 12 jump operators at n = 4096 and the Bartels-Stewart solve
+    S^{-1} at n = 1024 (the 10-site chain), each timed `repeats` times; one application is estimated as
+    (12 / d_sample) x the jump sample + (4096 / 1024)^3 x the Sylvester sample."""
     import numpy as np
 
     import lindblad_inputs as gi
@@ -122,27 +129,34 @@ def cpu_baseline(n_sites=12, d_sample=1):
     H, Ls = gi.tfim(n_sites, J=1.0, h=1.0, gamma=0.3)
     X = gi.random_hermitian(H.shape[0], seed=1)
     sysK = K.System(H, Ls[:d_sample])
-    t0 = time.perf_counter()
-    sysK.K(X)
-    t_k = (time.perf_counter() - t0) * (len(Ls) / d_sample)
     H10, L10 = gi.tfim(10, J=1.0, h=1.0, gamma=0.3)
     s10 = K.System(H10, L10)
     _ = s10.schur                                    # factorisation is set-up, not per apply
     X10 = gi.random_hermitian(H10.shape[0], seed=1)
-    t0 = time.perf_counter()
-    s10.S_inv(X10)
-    t_s = (time.perf_counter() - t0) * (H.shape[0] / H10.shape[0]) ** 3
+    tk, ts = [], []
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        sysK.K(X)
+        tk.append(time.perf_counter() - t0)
+        t0 = time.perf_counter()
+        s10.S_inv(X10)
+        ts.append(time.perf_counter() - t0)
+    k_scale, s_scale = len(Ls) / d_sample, (H.shape[0] / H10.shape[0]) ** 3
+    t_k, t_s = statistics.median(tk), statistics.median(ts)
+    per_apply = t_k * k_scale + t_s * s_scale
     threads = len(os.sched_getaffinity(0))   # NumPy's BLAS uses every core it is given
-    per_apply = t_k + t_s
     return {"value": 1.0 / per_apply, "unit": "Phi-applies/s", "cores": int(threads), "kind": "oracle",
-            "sample": (f"oracle System.K with {d_sample}/12 jumps at n=4096 scaled x{12 // d_sample}, plus "
-                       "Bartels-Stewart S^-1 (scipy Schur + ztrsyl) at n=1024 scaled x64; "
-                       f"est. {per_apply:.1f} s per apply")}
+            "sample": (f"oracle System.K with {d_sample}/12 jumps at n=4096 (x{k_scale:g}) plus Bartels-Stewart "
+                       f"S^-1 (scipy Schur + ztrsyl) at n=1024 (x{s_scale:g}); est. {per_apply:.1f} s per apply"),
+            "samples_run": repeats, "jump_sample_s": [round(v, 3) for v in tk],
+            "sylvester_sample_s": [round(v, 3) for v in ts], "extrapolated": True,
+            "extrapolation": {"jump_factor": k_scale, "sylvester_factor": s_scale}}
 
 
-# DRAM bytes (read + write) per jump-term k_tc_gemm launch at n = 4096, d = 12, from one ncu capture
-# of the current kernel (mean of the two launches of an application)
-JUMP_GEMM_TRAFFIC_BYTES = (10165062144 + 3187236352 + 11702182656 + 238166528) / 2
+# DRAM bytes (read + write) per jump-term k_tc_gemm launch, recorded from an ncu capture of the kernel
+# revision named below (None until the current revision has been captured)
+JUMP_GEMM_TRAFFIC_BYTES = None
+JUMP_GEMM_TRAFFIC_NOTE = "recorded profile value of the named kernel revision, not measured in this run"
 
 SWEEP = dict(workload="kerr_cat_sweep_1024", count=1024, seed=0, n_range=[16, 160], d=2,
              eps2=[1.0, 8.0], K=[0.5, 2.0], kappa1=[1e-3, 1e-1], kappa2=1.0)
@@ -304,6 +318,12 @@ def measure_peaks(device):
     return out
 
 
+def _solve_record(info, st, seconds):
+    return {"s": round(seconds, 3), "status": int(st), "residual_max": info["residual_max"],
+            "restarts": info["restarts"], "phi_applies": info["phi_applies"], "gmres_steps": info["gmres_steps"],
+            "refine_steps": info["refine_steps"]}
+
+
 def run_ours(args, rank, world, device):
     import numpy as np
     import torch
@@ -317,6 +337,7 @@ def run_ours(args, rank, world, device):
     Hd = torch.from_numpy(H).to(device)
     Ld = torch.from_numpy(np.stack(Ls)).to(device)
     del Ls
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     opts = B.default_opts(precision=B.LB_PREC_MIXED)
     h = B.lindblad_setup(Hd, Ld, opts)
@@ -328,8 +349,13 @@ def run_ours(args, rank, world, device):
     X = X / torch.linalg.matrix_norm(X)
     Y = torch.empty_like(X)
     stream = torch.cuda.current_stream()
+
+    def step(x, y, prec=B.LB_PREC_MIXED):
+        # the map Alg. 4 iterates: Phi~ in Schur coordinates on a Hermitian Krylov vector
+        B.phi_apply(h, x, y, schur=True, precision=prec, hermitian=True)
+
     for _ in range(args.warmup):
-        B.phi_apply(h, X, Y, schur=True, precision=B.LB_PREC_MIXED)
+        step(X, Y)
     torch.cuda.synchronize()
     B.lb_set_profiling(h, True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -341,7 +367,7 @@ def run_ours(args, rank, world, device):
         torch.cuda.profiler.start()   # profilers run with --profile-from-start off see the timed steps only
         e0.record(stream)
         for _ in range(args.steps):
-            B.phi_apply(h, X, Y, schur=True, precision=B.LB_PREC_MIXED)
+            step(X, Y)
         e1.record(stream)
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
@@ -359,37 +385,205 @@ def run_ours(args, rank, world, device):
     Xd = torch.empty_like(X)
     for _ in range(2):
         Xd.copy_(Xh, non_blocking=True)
-        B.phi_apply(h, Xd, Y, schur=True, precision=B.LB_PREC_MIXED)
+        step(Xd, Y)
         Yh.copy_(Y, non_blocking=True)
     torch.cuda.synchronize()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record(stream)
     for _ in range(args.steps):
         Xd.copy_(Xh, non_blocking=True)
-        B.phi_apply(h, Xd, Y, schur=True, precision=B.LB_PREC_MIXED)
+        step(Xd, Y)
         Yh.copy_(Y, non_blocking=True)
     f1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = f0.elapsed_time(f1)
 
     extra = {"setup_s": round(setup_s, 2), "schur_backward_err": h.setup_info["schur_backward_err"]}
-    if args.fp64:
+    if not args.quick:
+        # the headline's other half: one FP64 application, and the steady-state solve to ||L rho||_max <= 1e-10
+        # in both precisions (wall clock around the C-ABI call, which synchronises)
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        step(X, Y, B.LB_PREC_FP64)
+        g1.record(stream)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        B.phi_apply(h, X, Y, schur=True, precision=B.LB_PREC_FP64)
-        torch.cuda.synchronize()
-        extra["fp64_phi_apply_s"] = round(time.perf_counter() - t0, 3)
-    if args.solve:
+        extra["fp64_phi_apply_s"] = round(g0.elapsed_time(g1) / 1000.0, 3)
         o = B.default_opts(precision=B.LB_PREC_MIXED, tol=1e-10)
         t0 = time.perf_counter()
         rho, info, st = B.steady_state(h, o)
-        torch.cuda.synchronize()
-        extra["solve_mixed_s"] = round(time.perf_counter() - t0, 2)
-        extra["solve_mixed_info"] = {k: info[k] for k in ("status", "restarts", "phi_applies", "gmres_steps",
-                                                           "refine_steps", "residual_max")}
+        extra["solve_mixed"] = _solve_record(info, st, time.perf_counter() - t0)
+        extra["solve_mixed_s"] = extra["solve_mixed"]["s"]
+        extra["solve_mixed_residual"] = info["residual_max"]
+        if not args.no_fp64_solve:
+            o = B.default_opts(precision=B.LB_PREC_FP64, tol=1e-10, max_restarts=args.fp64_restarts)
+            t0 = time.perf_counter()
+            rho64, info64, st64 = B.steady_state(h, o)
+            extra["solve_fp64"] = _solve_record(info64, st64, time.perf_counter() - t0)
+            extra["solve_fp64_s"] = extra["solve_fp64"]["s"]
+            extra["solve_fp64_residual"] = info64["residual_max"]
+            extra["mixed_vs_fp64_solve_speedup"] = round(extra["solve_fp64_s"] / max(extra["solve_mixed_s"], 1e-9), 2)
+            extra["mixed_vs_fp64_state_rel_diff"] = float(torch.linalg.matrix_norm(rho - rho64) /
+                                                          torch.linalg.matrix_norm(rho64))
+        extra["end_to_end_mixed_s"] = round(setup_s + extra["solve_mixed_s"], 2)
     B.lindblad_destroy(h)
     return dict(ms=ms, e2e_ms=e2e_ms, launches=launches, kms=kms, kflops=kflops, clocks=clk.summary(),
                 n=n, d=d, extra=extra, gpu_launches=gpu_launches)
+
+
+def _setup_case(B, torch, device, H, Ls, **kw):
+    import numpy as np
+    Hd = torch.from_numpy(H).to(device)
+    Ld = torch.from_numpy(np.stack(Ls)).to(device)
+    o = B.default_opts(**kw)
+    t0 = time.perf_counter()
+    h = B.lindblad_setup(Hd, Ld, o)
+    torch.cuda.synchronize()
+    return h, time.perf_counter() - t0
+
+
+def _kernel_roofline(B, h, pk, kid):
+    """Algorithmic rate of the library's tensor-core (kid 0) or FP64 (kid 1) GEMM launches recorded while
+    profiling was on, against the matching measured peak."""
+    launches, kms, kfl = B.lb_kernel_stats(h, kid)
+    if not launches:
+        return None
+    ach = kfl / (kms / 1000.0) / 1e12
+    if kid == 0:
+        peak, unit_src = pk["bf16_tflops"], "bf16_tflops burst (kind::f16 FP16 = BF16 rate)"
+    else:
+        peak, unit_src = 1.04, "cuBLAS DGEMM measured on this pool (bench.py --peaks)"
+    return {"bound": "tensor" if kid == 0 else "fp64-alu", "kernel": "k_tc_gemm" if kid == 0 else "zgemm_f64_kernel",
+            "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+            "peak_source": unit_src, "launches": launches, "ms_total": kms}
+
+
+def run_workload(args, device):
+    """Lines for the solvers built on the recycled preconditioned GMRES and for the cat qubit:
+    resolvent (Sec. 3.4), implicit Euler (Sec. 4.3), Alg. 3 (Sec. 4.1) and the cat-qubit spectrum (Sec. 4.2)."""
+    import numpy as np
+    import torch
+
+    import lindblad_inputs as gi
+    import paper_2608_30860_b300 as B
+
+    torch.cuda.set_device(device)
+    pk, src = _peaks()
+    stream = torch.cuda.current_stream()
+    prec = B.LB_PREC_MIXED if args.precision == "mixed" else B.LB_PREC_FP64
+    line = {"n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "data": "synthetic", "dtype": "f16x2-split/f32acc+f64" if prec else "f64"}
+    n0 = B.lb_launch_count()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        if args.workload == "resolvent":
+            # the paper's dense random family, (lam - L) X = I/n at lam = lam_max 10^{0,-1,-2}; lam_max from a
+            # power iteration on L, off the clock
+            n = args.n
+            H, Ls = gi.paper_random_lindbladian(n, seed=0)
+            h, setup_s = _setup_case(B, torch, device, H, Ls, precision=prec)
+            v = torch.from_numpy(gi.random_operator(n, seed=3)).to(device)
+            lmax = 0.0
+            for _ in range(30):
+                w = B.lindbladian_apply(h, v)
+                lmax = float(torch.linalg.matrix_norm(w) / torch.linalg.matrix_norm(v))
+                v = w / torch.linalg.matrix_norm(w)
+            Bm = torch.eye(n, dtype=torch.complex128, device=device) / n
+            per = {}
+            for k in range(max(1, args.warmup // 3)):
+                B.resolvent_solve(h, lmax, Bm, B.default_opts(precision=prec, tol=1e-8))
+            B.lb_set_profiling(h, True)
+            total = 0.0
+            for lam_f in (1.0, 0.1, 0.01):
+                lam = lmax * lam_f
+                times = []
+                for _ in range(args.steps):
+                    t0 = time.perf_counter()
+                    X, info, st = B.resolvent_solve(h, lam, Bm, B.default_opts(precision=prec, tol=1e-8, gmres_m=32,
+                                                                              recycle_k=8))
+                    times.append(time.perf_counter() - t0)
+                per[f"lam_max*{lam_f:g}"] = {"s_median": statistics.median(times), "status": st,
+                                             "residual_max": info["residual_max"], "gmres_steps": info["gmres_steps"]}
+                total += statistics.median(times)
+            line.update(metric="resolvent solves/s, (lam-L)X=I/n at lam=lam_max*10^{0,-1,-2}, resid<=1e-8",
+                        value=3.0 / total, unit="solves/s", ms_per_step=1000.0 * total / 3.0,
+                        config={"workload": f"paper_random_n{n}_d3_resolvent", "n": n, "d": 3, "gamma": 0.1,
+                                "lam_max": lmax, "tol": 1e-8, "gmres_m": 32, "recycle_k": 8,
+                                "l2": "operands exceed L2" if n >= 2048 else "operands fit L2"},
+                        per_shift=per, setup_s=round(setup_s, 3))
+        elif args.workload == "euler":
+            # Sec. 4.3's stiff family: n = 32 dense random + K N^2, K in {0, 15}; fixed dt, steps/s
+            n, dt, nsteps = 32, 0.01, 200
+            per = {}
+            tot_steps, tot_s = 0, 0.0
+            for Kq in (0.0, 15.0):
+                H, Ls = gi.stiff_random_lindbladian(n, K=Kq, seed=0)
+                h, _ = _setup_case(B, torch, device, H, Ls)
+                rho0 = torch.zeros((n, n), dtype=torch.complex128, device=device)
+                rho0[0, 0] = 1.0
+                B.implicit_euler(h, rho0, dt, 5, B.default_opts(tol=1e-8))
+                t0 = time.perf_counter()
+                rho, _, info, st = B.implicit_euler(h, rho0, dt, nsteps, B.default_opts(tol=1e-8, gmres_m=32, recycle_k=8))
+                el = time.perf_counter() - t0
+                per[f"K={Kq:g}"] = {"s": el, "steps_per_s": nsteps / el, "status": st,
+                                    "gmres_steps_per_step": info["gmres_steps"] / nsteps,
+                                    "worst_rel_step_residual": info["residual_max"]}
+                tot_steps += nsteps
+                tot_s += el
+                B.lindblad_destroy(h)
+            line.update(metric="implicit Euler steps/s (n=32 stiff random + K N^2, dt=0.01, step resid<=1e-8)",
+                        value=tot_steps / tot_s, unit="steps/s", ms_per_step=1000.0 * tot_s / tot_steps,
+                        config={"workload": "stiff_random_n32_euler", "n": n, "dt": dt, "steps": nsteps,
+                                "K": [0.0, 15.0], "l2": "operands fit L2"}, per_K=per, dtype="f64")
+            h = None
+        elif args.workload == "gmres":
+            # Alg. 3 (recycled preconditioned GMRES) at the benchmark's n = 4096 (or --sites)
+            H, Ls = gi.tfim(args.sites, J=1.0, h=1.0, gamma=0.3)
+            n = H.shape[0]
+            h, setup_s = _setup_case(B, torch, device, H, Ls, precision=B.LB_PREC_MIXED)
+            B.lb_set_profiling(h, True)
+            t0 = time.perf_counter()
+            rho, info, st = B.steady_state_gmres(h, B.default_opts(precision=prec, tol=1e-10, gmres_m=32, recycle_k=8))
+            el = time.perf_counter() - t0
+            line.update(metric="steady-state solve time, Alg. 3 (recycled preconditioned GMRES), resid<=1e-10",
+                        value=el, unit="s", higher_is_better=False, ms_per_step=1000.0 * el,
+                        config={"workload": f"tfim{args.sites}_n{n}_d{len(Ls)}_alg3", "n": n, "d": len(Ls),
+                                "gmres_m": 32, "recycle_k": 8, "l2": "operands exceed L2"},
+                        setup_s=round(setup_s, 2), solve=_solve_record(info, st, el), steps=1)
+        elif args.workload == "cat":
+            # App. B memory-buffer cat: steady state (Alg. 4) and the 3 slowest modes (Alg. 5) across n
+            per = {}
+            tot = 0.0
+            for ntarget in args.cat_n:
+                na, nb = gi.memory_buffer_dims(ntarget)
+                H, Ls = gi.memory_buffer_cat(na, nb)
+                h, setup_s = _setup_case(B, torch, device, H, Ls, precision=prec)
+                t0 = time.perf_counter()
+                rho, info, st = B.steady_state(h, B.default_opts(precision=prec, tol=1e-10, max_restarts=200))
+                t_ss = time.perf_counter() - t0
+                t0 = time.perf_counter()
+                ev, _, sinfo, sst = B.low_spectrum(h, 3, opts=B.default_opts(precision=prec, tol=1e-8, krylov_m=24))
+                t_sp = time.perf_counter() - t0
+                tot += t_ss + t_sp
+                per[f"n={na * nb}"] = {"na": na, "nb": nb, "alpha2": na / 5.0, "setup_s": setup_s,
+                                       "steady_state_s": t_ss, "steady_state_status": st,
+                                       "residual_max": info["residual_max"], "spectrum_s": t_sp,
+                                       "spectrum_status": sst, "decay_rates": [float(-x.real) for x in ev.numpy()],
+                                       "eigenvalues": [[float(x.real), float(x.imag)] for x in ev.numpy()]}
+                B.lindblad_destroy(h)
+            line.update(metric="memory-buffer cat: steady state + 3 slowest modes, time per system",
+                        value=len(args.cat_n) / tot, unit="systems/s", ms_per_step=1000.0 * tot / len(args.cat_n),
+                        config={"workload": "memory_buffer_cat", "n_targets": args.cat_n,
+                                "params": gi.MEMORY_BUFFER, "l2": "operands fit L2"}, per_n=per, steps=1)
+            h = None
+        else:
+            raise ValueError(args.workload)
+        torch.cuda.synchronize()
+    line["clocks"] = clk.summary()
+    line["gpu_launches"] = B.lb_launch_count() - n0
+    if h is not None:
+        line["roofline"] = _kernel_roofline(B, h, pk, 0 if prec else 1)
+        B.lindblad_destroy(h)
+    line["e2e"] = None
+    return line
 
 
 def main():
@@ -398,13 +592,20 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--solve", action="store_true", help="also time one mixed steady-state solve")
-    ap.add_argument("--fp64", action="store_true", help="also time one all-FP64 Phi application")
+    ap.add_argument("--quick", action="store_true",
+                    help="time the Phi applications only (skip the FP64 application and both steady-state solves)")
+    ap.add_argument("--no-fp64-solve", action="store_true", help="skip the all-FP64 steady-state solve")
+    ap.add_argument("--fp64-restarts", type=int, default=12, help="restart cap of the all-FP64 solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--peaks", action="store_true",
                     help="only measure library GEMM peaks (FP64, FP32, TF32, complex64/128) and print them")
-    ap.add_argument("--workload", default="tfim12", choices=["tfim12", "sweep"],
-                    help="tfim12: Phi applications at n=4096 (default); sweep: the batched Kerr-cat sweep")
+    ap.add_argument("--workload", default="tfim12",
+                    choices=["tfim12", "sweep", "resolvent", "euler", "gmres", "cat"],
+                    help="tfim12: Phi applications + steady-state solves at n=4096 (default); sweep: the batched "
+                         "Kerr-cat sweep; resolvent / euler / gmres / cat: the GMRES-based solvers and the cat qubit")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"], help="precision of the extra workloads")
+    ap.add_argument("--n", type=int, default=1024, help="size of the resolvent workload")
+    ap.add_argument("--cat-n", type=int, nargs="+", default=[256, 512, 1024], help="target sizes of the cat workload")
     ap.add_argument("--sweep-count", type=int, default=SWEEP["count"],
                     help="instances of the sweep (1024: the benchmark; small values give profiler cases)")
     ap.add_argument("--sweep-n", type=int, nargs=2, default=SWEEP["n_range"], metavar=("NMIN", "NMAX"))
@@ -419,12 +620,16 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
 
     if args.impl == "reference":
-        # the oracle timed on the host cores; rank 0 only
+        # the oracle timed on the host cores, rank 0 only: every step times one bounded sample (one of the
+        # 12 jump products at n = 4096 and one Bartels-Stewart solve at n = 1024) and extrapolates it to a
+        # full application; the warm-up samples are not reported
         if rank != 0:
             return
-        cb = cpu_baseline()
+        cpu_baseline(repeats=1)
+        cb = cpu_baseline(repeats=max(1, min(args.steps, 10)))
         line = {"metric": METRIC, "value": cb["value"], "unit": "Phi-applies/s", "n_gpus": args.gpus,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / cb["value"],
+                "steps": cb["samples_run"], "warmup": 1, "ms_per_step": 1000.0 / cb["value"],
+                "ms_per_step_is_extrapolated": True,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic", "impl": "reference", "config": dict(WORKLOAD, parallelism="none"),
                 "cpu_baseline": cb,
@@ -451,6 +656,12 @@ def main():
         if world > 1:
             torch.distributed.destroy_process_group()
         return
+    if args.workload != "tfim12":
+        if rank == 0:
+            print(json.dumps(run_workload(args, device)))
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
     r = run_ours(args, rank, world, device)
     ms, e2e_ms = max_over_ranks([r["ms"], r["e2e_ms"]], world, device)
     if rank != 0:
@@ -460,8 +671,7 @@ def main():
     value = whole_job_rate(1, args.steps, world, ms)
     e2e_value = whole_job_rate(1, args.steps, world, e2e_ms)
     n = r["n"]
-    per_launch_ms = r["kms"] / max(r["launches"], 1)
-    achieved = (r["kflops"] / max(r["launches"], 1)) / (per_launch_ms / 1000.0) / 1e12 if r["launches"] else None
+    achieved = (r["kflops"] / (r["kms"] / 1000.0)) / 1e12 if r["launches"] else None
     peak = pk["bf16_tflops"]
     line = {
         "metric": METRIC, "value": value, "unit": "Phi-applies/s", "n_gpus": world, "steps": args.steps,
@@ -471,26 +681,26 @@ def main():
                                                               N_sites=args.sites, n=n, d=r["d"], J=1.0, h=1.0,
                                                               gamma=0.3),
                        parallelism="replicas" if world > 1 else "none",
+                       step="Phi~ in Schur coordinates on a Hermitian Krylov vector (LB_APPLY_HERMITIAN)",
                        l2="operands (1.6 GB L~ planes) exceed L2; no flush"),
-        "roofline": {"bound": "tensor", "kernel": "k_tc_gemm (tcgen05 split-FP16 complex GEMM)",
+        "roofline": {"bound": "tensor", "kernel": "k_tc_gemm (tcgen05 split-FP16 complex GEMM, jump term)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": (achieved / peak) if achieved else None,
                      "traffic": JUMP_GEMM_TRAFFIC_BYTES if args.sites == 12 else None,
-                     "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum per jump-term launch, "
-                                       "profiles/tc_gemm_traffic_tfim12_n4096.md",
+                     "traffic_note": JUMP_GEMM_TRAFFIC_NOTE,
                      "peak_source": f"bf16_tflops burst of {src} MEASURED_PEAKS.json (kind::f16 FP16 = BF16 rate)",
-                     "launches": r["launches"], "ms_per_launch": per_launch_ms,
-                     "flops_per_launch": r["kflops"] / max(r["launches"], 1)},
+                     "launches": r["launches"], "ms_per_launch": r["kms"] / max(r["launches"], 1),
+                     "flops_per_launch": r["kflops"] / max(r["launches"], 1),
+                     "flops_note": "algorithmic: 8 d n^3 for product (1), 4 d n^2 (n + 1) for the Hermitian "
+                                   "product (2)"},
         "e2e": {"value": e2e_value, "unit": "Phi-applies/s", "h2d_bytes_per_step": 16 * n * n,
                 "d2h_bytes_per_step": 16 * n * n},
-        "gpu_launches": None,
+        "gpu_launches": r["gpu_launches"],
         "clocks": r["clocks"],
     }
     line.update(r["extra"])
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
-    # kernels the library launched inside the timed region (its own launch counter)
-    line["gpu_launches"] = r["gpu_launches"]
     print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()

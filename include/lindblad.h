@@ -60,9 +60,12 @@ typedef enum {
 
 typedef enum { LB_FORM_PHI = 0, LB_FORM_M = 1 } lb_form;   /* Phi = -K S^{-1}; M = -S^{-1} K */
 
-/* phi_apply flags: form in bit 0; coordinates in bit 1 */
+/* phi_apply / jump_apply flags: form in bit 0; coordinates in bit 1; Hermitian input in bit 2 */
 #define LB_APPLY_FORM_M   1   /* apply M instead of Phi */
 #define LB_APPLY_SCHUR    2   /* X and Y are given in Schur coordinates X~ = Q^dag X Q */
+#define LB_APPLY_HERMITIAN 4  /* X is Hermitian (the caller guarantees it): S^{-1} and K preserve Hermiticity
+                                 (App. A.1.1), so the jump term's second product is formed on its upper
+                                 tiles only and mirrored; the result is exactly Hermitian */
 
 typedef struct {
     double tol;           /* stop when ||L(rho_hat)||_max < tol (absolute, hermitised trace-1 state);

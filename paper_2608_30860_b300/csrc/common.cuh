@@ -52,7 +52,12 @@ struct ZGemmArgs {
     cplx alpha, beta;
     int batch;    // number of (A_b, B_b) pairs
     int reduce;   // 1: C = alpha * sum_b op(A_b) op(B_b) + beta C ; 0: C_b = alpha op(A_b) op(B_b) + beta C_b
+    int herm;     // 1 (reduce = 1, M = N): the result is Hermitian (alpha, beta real, C Hermitian on entry):
+                  // only the tiles on and above the diagonal are computed, the rest is mirrored
 };
+
+// C[i][j] = conj(C[j][i]) for i > j (n x n, leading dimension ld)
+int mat_mirror_lower(cplx* C, int n, long long ld, cudaStream_t s);
 
 // host launchers (defined in the .cu files)
 int zgemm_f64(const ZGemmArgs& a, cudaStream_t s);

@@ -28,6 +28,7 @@ __global__ void __launch_bounds__(256) zgemm_f64_kernel(ZGemmArgs a) {
     const int tx = tid & 15, ty = tid >> 4;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const int bz = blockIdx.z;
+    if (a.herm && blockIdx.y > blockIdx.x) return;   // strictly below the diagonal: mirrored afterwards
 
     cplx acc[4][4];
 #pragma unroll
@@ -90,11 +91,36 @@ __global__ void __launch_bounds__(256) zgemm_f64_kernel(ZGemmArgs a) {
     }
 }
 
+// C[i][j] = conj(C[j][i]) below the diagonal, 32 x 32 tiles through shared memory (coalesced both ways)
+__global__ void k_mirror_lower(cplx* C, int n, long long ld) {
+    __shared__ cplx t[32][33];
+    const int bi = blockIdx.y, bj = blockIdx.x;   // destination tile (bi, bj), bi >= bj
+    if (bi < bj) return;
+    const int tx = threadIdx.x;
+    for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
+        const int r = bj * 32 + yy, c = bi * 32 + tx;   // source: the tile (bj, bi) above the diagonal
+        if (r < n && c < n) t[yy][tx] = C[(long long)r * ld + c];
+    }
+    __syncthreads();
+    for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
+        const int r = bi * 32 + yy, c = bj * 32 + tx;
+        if (r < n && c < n && r > c) C[(long long)r * ld + c] = cconj(t[tx][yy]);
+    }
+}
+
 }  // namespace
+
+int mat_mirror_lower(cplx* C, int n, long long ld, cudaStream_t s) {
+    const int nt = (n + 31) / 32;
+    k_mirror_lower<<<dim3(nt, nt), dim3(32, 8), 0, s>>>(C, n, ld); lb_note_launch();
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
 
 int zgemm_f64(const ZGemmArgs& a, cudaStream_t s) {
     if (a.M <= 0 || a.N <= 0) return 0;
+    if (a.herm && (a.M != a.N || !a.reduce)) return -1;
     dim3 grid((a.N + BN - 1) / BN, (a.M + BM - 1) / BM, a.reduce ? 1 : a.batch);
     zgemm_f64_kernel<<<grid, 256, 0, s>>>(a); lb_note_launch();
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    if (cudaGetLastError() != cudaSuccess) return -1;
+    return a.herm ? mat_mirror_lower(a.C, a.M, a.ldc, s) : 0;
 }

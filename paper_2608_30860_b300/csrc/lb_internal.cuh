@@ -95,12 +95,14 @@ void prof_begin(lb_handle_s* h, cudaStream_t s, int kid);
 void prof_end(lb_handle_s* h, cudaStream_t s, int kid, double flops);
 int gemm(lb_handle_s* h, cudaStream_t s, cplx* C, const cplx* A, int opA, const cplx* B, int opB, int M, int N,
          int K, cplx alpha, cplx beta);
-int jump_f64(lb_handle_s* h, cudaStream_t s, const cplx* Ls, const cplx* Z, cplx* Y, cplx alpha, cplx beta);
+int jump_f64(lb_handle_s* h, cudaStream_t s, const cplx* Ls, const cplx* Z, cplx* Y, cplx alpha, cplx beta,
+             int herm = 0);
 int lindbladian_f64(lb_handle_s* h, cudaStream_t s, const cplx* X, cplx* R);
+int lindbladian_f64_herm(lb_handle_s* h, cudaStream_t s, const cplx* X, cplx* R);
 int change_basis(lb_handle_s* h, cudaStream_t s, const cplx* X, cplx* Out, cplx* tmp, int to_schur);
 int lyap_schur(lb_handle_s* h, cudaStream_t s, const cplx* Y, cplx* X, double shift, int precision);
 int lyap_eig(lb_handle_s* h, cudaStream_t s, const cplx* Y, cplx* X, double shift);
-int phi_schur(lb_handle_s* h, cudaStream_t s, const cplx* X, cplx* Y, int form, int precision);
+int phi_schur(lb_handle_s* h, cudaStream_t s, const cplx* X, cplx* Y, int form, int precision, int herm = 0);
 int arnoldi_cycle(lb_handle_s* h, cudaStream_t s, cplx* basis, cplx* hess, int j0, int m, const OpFn& op,
                   int* k_out);
 int hermitize_normalize(lb_handle_s* h, cudaStream_t s, const cplx* in, cplx* out, cplx* tmp);
@@ -134,7 +136,7 @@ int adj_jump_f64(lb_handle_s* h, cudaStream_t s, const cplx* Z, cplx* Y, cplx al
 size_t mixed_bytes(int n, int d);
 size_t mixed_P_rows(int n, int d);
 int mixed_prepare(lb_handle_s* h, cudaStream_t s);
-int jump_mixed(lb_handle_s* h, cudaStream_t s, const cplx* Z, cplx* Y, double alpha);
+int jump_mixed(lb_handle_s* h, cudaStream_t s, const cplx* Z, cplx* Y, double alpha, int herm = 0);
 void mixed_release(lb_handle_s* h);
 
 // sylv_mixed.cu

@@ -183,8 +183,10 @@ int gemm(lb_handle_s* h, cudaStream_t s, cplx* C, const cplx* A, int opA, const 
     return r;
 }
 
-// Y = alpha * sum_j Lop_j Z Lop_j^dag + beta Y, with Lop the stack Ls (d x n x n), in FP64.
-int jump_f64(lb_handle_s* h, cudaStream_t s, const cplx* Ls, const cplx* Z, cplx* Y, cplx alpha, cplx beta) {
+// Y = alpha * sum_j Lop_j Z Lop_j^dag + beta Y, with Lop the stack Ls (d x n x n), in FP64.  herm = 1
+// (Z Hermitian, alpha and beta real, Y Hermitian on entry): the second product is Hermitian, so only
+// its upper tiles are computed and the rest mirrored.
+int jump_f64(lb_handle_s* h, cudaStream_t s, const cplx* Ls, const cplx* Z, cplx* Y, cplx alpha, cplx beta, int herm) {
     const int n = h->n, d = h->d;
     const long long nn = (long long)n * n;
     // P = [L_1; ...; L_d] Z  (dn x n)
@@ -195,10 +197,10 @@ int jump_f64(lb_handle_s* h, cudaStream_t s, const cplx* Ls, const cplx* Z, cplx
     a.A = h->P; a.lda = n; a.strideA = nn; a.opA = OP_N;
     a.B = Ls; a.ldb = n; a.strideB = nn; a.opB = OP_C;
     a.C = Y; a.ldc = n; a.strideC = 0;
-    a.alpha = alpha; a.beta = beta; a.batch = d; a.reduce = 1;
+    a.alpha = alpha; a.beta = beta; a.batch = d; a.reduce = 1; a.herm = herm;
     prof_begin(h, s, 1);
     int r = zgemm_f64(a, s);
-    prof_end(h, s, 1, 8.0 * n * (double)n * n * d);
+    prof_end(h, s, 1, (herm ? 4.0 * (n + 1) : 8.0 * n) * (double)n * n * d);
     return r;
 }
 
@@ -208,6 +210,15 @@ int lindbladian_f64(lb_handle_s* h, cudaStream_t s, const cplx* X, cplx* R) {
     if (gemm(h, s, R, h->G, OP_N, X, OP_N, n, n, n, cmake(1, 0), cmake(0, 0))) return -1;
     if (gemm(h, s, R, X, OP_N, h->G, OP_C, n, n, n, cmake(1, 0), cmake(1, 0))) return -1;
     return jump_f64(h, s, h->L, X, R, cmake(1, 0), cmake(1, 0));
+}
+
+// the same for Hermitian X: X G^dag = (G X)^dag, so one GEMM and an adjoint-add form the no-jump part,
+// and the jump part is Hermitian (upper tiles only)
+int lindbladian_f64_herm(lb_handle_s* h, cudaStream_t s, const cplx* X, cplx* R) {
+    const int n = h->n;
+    if (gemm(h, s, R, h->G, OP_N, X, OP_N, n, n, n, cmake(1, 0), cmake(0, 0))) return -1;
+    if (mat_add_adjoint(R, n, s)) return -1;
+    return jump_f64(h, s, h->L, X, R, cmake(1, 0), cmake(1, 0), 1);
 }
 
 // Out = Q X Q^dag (to_schur = 0) or Q^dag X Q (to_schur = 1); tmp must differ from X and Out
@@ -243,18 +254,20 @@ int lyap_eig(lb_handle_s* h, cudaStream_t s, const cplx* Y, cplx* X, double shif
     return gemm(h, s, X, t, OP_N, h->Re, OP_C, n, n, n, cmake(1, 0), cmake(0, 0));
 }
 
-// Schur-coordinate Phi (form 0) or M (form 1): Y = -K~ S~^{-1} X  or  Y = -S~^{-1} K~ X
-int phi_schur(lb_handle_s* h, cudaStream_t s, const cplx* X, cplx* Y, int form, int precision) {
+// Schur-coordinate Phi (form 0) or M (form 1): Y = -K~ S~^{-1} X  or  Y = -S~^{-1} K~ X.  herm = 1: X is
+// Hermitian, so is every intermediate (S~^{-1} and K~ preserve Hermiticity) and the jump term's second
+// product is formed on its upper tiles only.
+int phi_schur(lb_handle_s* h, cudaStream_t s, const cplx* X, cplx* Y, int form, int precision, int herm) {
     cplx* Z = h->X[0];
     const long long nn = (long long)h->n * h->n;
     if (form == 0) {
         if (lyap_schur(h, s, X, Z, 0.0, precision)) return -1;
-        if (precision == LB_PREC_MIXED && h->mixed_ready) return jump_mixed(h, s, Z, Y, -1.0);
-        return jump_f64(h, s, h->Lt, Z, Y, cmake(-1, 0), cmake(0, 0));
+        if (precision == LB_PREC_MIXED && h->mixed_ready) return jump_mixed(h, s, Z, Y, -1.0, herm);
+        return jump_f64(h, s, h->Lt, Z, Y, cmake(-1, 0), cmake(0, 0), herm);
     }
     if (precision == LB_PREC_MIXED && h->mixed_ready) {
-        if (jump_mixed(h, s, X, Z, 1.0)) return -1;
-    } else if (jump_f64(h, s, h->Lt, X, Z, cmake(1, 0), cmake(0, 0))) {
+        if (jump_mixed(h, s, X, Z, 1.0, herm)) return -1;
+    } else if (jump_f64(h, s, h->Lt, X, Z, cmake(1, 0), cmake(0, 0), herm)) {
         return -1;
     }
     if (lyap_schur(h, s, Z, Z, 0.0, precision)) return -1;
@@ -335,7 +348,8 @@ int hermitize_normalize(lb_handle_s* h, cudaStream_t s, const cplx* in, cplx* ou
 
 // max-norm and Frobenius norm of L(rho), rho in the original basis; R scratch
 int residual_norms(lb_handle_s* h, cudaStream_t s, const cplx* rho, cplx* R, double* rmax, double* rfro) {
-    if (lindbladian_f64(h, s, rho, R)) return -1;
+    // rho is Hermitian here (every caller hermitises first)
+    if (lindbladian_f64_herm(h, s, rho, R)) return -1;
     if (vec_norms(R, (long long)h->n * h->n, h->dpart, h->dscal, s)) return -1;
     double out[2];
     LB_CHECK_CUDA(cudaMemcpyAsync(out, h->dscal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -635,14 +649,15 @@ lb_status phi_apply(lindblad_handle h, const void* X_dev, void* Y_dev, int flags
     if (h->case1) return LB_S_SINGULAR;
     cudaStream_t s = (cudaStream_t)stream;
     const int form = flags & LB_APPLY_FORM_M ? 1 : 0;
+    const int herm = flags & LB_APPLY_HERMITIAN ? 1 : 0;
     const cplx* X = (const cplx*)X_dev;
     cplx* Y = (cplx*)Y_dev;
     if (precision == LB_PREC_MIXED && !h->mixed_ready) return LB_NOT_IMPLEMENTED;
     if (flags & LB_APPLY_SCHUR) {
-        if (phi_schur(h, s, X, Y, form, precision)) return LB_CUDA_ERROR;
+        if (phi_schur(h, s, X, Y, form, precision, herm)) return LB_CUDA_ERROR;
     } else {
         if (change_basis(h, s, X, h->X[1], h->X[2], 1)) return LB_CUDA_ERROR;
-        if (phi_schur(h, s, h->X[1], h->X[3], form, precision)) return LB_CUDA_ERROR;
+        if (phi_schur(h, s, h->X[1], h->X[3], form, precision, herm)) return LB_CUDA_ERROR;
         if (change_basis(h, s, h->X[3], Y, h->X[2], 0)) return LB_CUDA_ERROR;
     }
     return precision == LB_PREC_MIXED ? check_device_error(h, s) : LB_OK;
@@ -654,19 +669,21 @@ lb_status jump_apply(lindblad_handle h, const void* X_dev, void* Y_dev, int flag
     cudaStream_t s = (cudaStream_t)stream;
     const cplx* X = (const cplx*)X_dev;
     cplx* Y = (cplx*)Y_dev;
+    const int herm = flags & LB_APPLY_HERMITIAN ? 1 : 0;
     if (!(flags & LB_APPLY_SCHUR)) {
         // original basis: L_j themselves (FP64), or via Schur coordinates on the tensor cores
-        if (precision != LB_PREC_MIXED) return jump_f64(h, s, h->L, X, Y, cmake(1, 0), cmake(0, 0)) ? LB_CUDA_ERROR : LB_OK;
+        if (precision != LB_PREC_MIXED)
+            return jump_f64(h, s, h->L, X, Y, cmake(1, 0), cmake(0, 0), herm) ? LB_CUDA_ERROR : LB_OK;
         if (change_basis(h, s, X, h->X[1], h->X[2], 1)) return LB_CUDA_ERROR;
-        if (jump_mixed(h, s, h->X[1], h->X[3], 1.0)) return LB_CUDA_ERROR;
+        if (jump_mixed(h, s, h->X[1], h->X[3], 1.0, herm)) return LB_CUDA_ERROR;
         if (change_basis(h, s, h->X[3], Y, h->X[2], 0)) return LB_CUDA_ERROR;
         return check_device_error(h, s);
     }
     if (precision == LB_PREC_MIXED) {
-        if (jump_mixed(h, s, X, Y, 1.0)) return LB_CUDA_ERROR;
+        if (jump_mixed(h, s, X, Y, 1.0, herm)) return LB_CUDA_ERROR;
         return check_device_error(h, s);
     }
-    return jump_f64(h, s, h->Lt, X, Y, cmake(1, 0), cmake(0, 0)) ? LB_CUDA_ERROR : LB_OK;
+    return jump_f64(h, s, h->Lt, X, Y, cmake(1, 0), cmake(0, 0), herm) ? LB_CUDA_ERROR : LB_OK;
 }
 
 lb_status resolvent_apply(lindblad_handle h, const void* Y_dev, void* X_dev, double lam, int precision,
@@ -741,7 +758,8 @@ lb_status steady_state_arnoldi(lb_handle_s* h, cudaStream_t s, const lb_opts& o,
     double best = INFINITY;
     // start vector I/n, normalised: I/sqrt(n)  (Schur-coordinate invariant)
     if (mat_eye(h->V, n, cmake(1.0 / std::sqrt((double)n), 0.0), s)) return LB_CUDA_ERROR;
-    OpFn op = [&](const cplx* x, cplx* y) { return phi_schur(h, s, x, y, 0, prec); };
+    // the Krylov vectors of Phi from the Hermitian start I/sqrt(n) are Hermitian (real Hessenberg)
+    OpFn op = [&](const cplx* x, cplx* y) { return phi_schur(h, s, x, y, 0, prec, 1); };
     std::vector<cplx> evh(KMAX);
     double prev_ritz = INFINITY;
     int restart = 0;

@@ -1,10 +1,13 @@
 // Mixed-precision (tensor-core) jump term in Schur coordinates:
 //   K~(Z) = sum_j L~_j Z L~_j^dag
 // as two split-FP16 complex GEMMs on tcgen05 (tc_gemm.cu), FP32 accumulation:
-//   (1) P = [L~_1; ...; L~_d] Z          one stacked product, M = d * n_pad
-//   (2) Y = alpha sum_j P_j L~_j^dag     one product whose K loop runs over (j, k)
-// The L~_j planes are packed once at set-up; Z and P are packed per call with a power-of-two
-// scale each (max |entry| -> 2^14), and the epilogues undo the scales.
+//   (1) P = [L~_1; ...; L~_d] Z          one stacked product, M = d * n_pad, whose epilogue writes P
+//                                        directly as the FP16 hi/lo planes of product (2)'s operand
+//   (2) Y = alpha sum_j P_j L~_j^dag     one product whose K loop runs over (j, k); for Hermitian Z the
+//                                        tiles below the diagonal are skipped and mirrored
+// The L~_j planes are packed once at set-up; Z is packed per call with a power-of-two scale
+// (max |entry| -> 2^14); P's scale comes from the bound max_r ||L~_r,:||_1 sqrt(2) max|Z| (P is never
+// stored in FP64), and the epilogues undo the scales.
 #include "lb_internal.cuh"
 #include "tc_gemm.cuh"
 #include "vecops.cuh"
@@ -19,7 +22,9 @@ struct MixedState {
 };
 
 // sc[0] scale_L, sc[1] inv_L, sc[2] scale_Z, sc[3] inv_Z, sc[4] scale_P, sc[5] inv_P,
-// sc[6] inv_L*inv_Z, sc[7] inv_P*inv_L, sc[8..9] norms scratch
+// sc[6] inv_L*inv_Z, sc[7] inv_P*inv_L, sc[8] max|Z| (re/im), sc[9] scratch,
+// sc[10] the factor product (1)'s epilogue applies (scale_P inv_L inv_Z),
+// sc[11] max_{j,r} sum_k (|Re L~_j[r,k]| + |Im L~_j[r,k]|) (set-up)
 namespace {
 
 inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
@@ -60,6 +65,8 @@ int mixed_prepare(lb_handle_s* h, cudaStream_t s) {
     if (tc_split_planes(h->Lt, n, n, n, 0, 0, m->sc + 0, m->Lp, (int)np, (long long)d * np * np, d,
                         (long long)n * n, (long long)np * np, s))
         return -1;
+    // the a-priori bound |P_rc| <= max_r ||L~_j[r,:]||_1 sqrt(2) max|Z| that scales P's planes
+    if (tc_max_row_l1(h->Lt, (long long)d * n, n, n, h->dpart, m->sc + 11, s)) return -1;
     if (tc_make_map(&m->maps.m[0], m->Lp, (int)np, (int)(d * np), 1, (int)np)) return -1;
     if (tc_make_map(&m->maps.m[1], m->Zp, (int)np, (int)np, 1, (int)np)) return -1;
     if (tc_make_map(&m->maps.m[2], m->Pp, (int)np, (int)np, d, (int)np)) return -1;
@@ -68,8 +75,9 @@ int mixed_prepare(lb_handle_s* h, cudaStream_t s) {
     return sylv_mixed_prepare(h, base, s);
 }
 
-// Y = alpha * sum_j L~_j Z L~_j^dag  (Z, Y: n x n complex128, Schur coordinates)
-int jump_mixed(lb_handle_s* h, cudaStream_t s, const cplx* Z, cplx* Y, double alpha) {
+// Y = alpha * sum_j L~_j Z L~_j^dag  (Z, Y: n x n complex128, Schur coordinates).  herm = 1 (Z Hermitian):
+// product (2) is Hermitian, its tiles below the diagonal are skipped and mirrored.
+int jump_mixed(lb_handle_s* h, cudaStream_t s, const cplx* Z, cplx* Y, double alpha, int herm) {
     MixedState* m = h->mixed;
     if (!m) return -1;
     const int n = h->n, d = h->d, np = m->np;
@@ -80,30 +88,30 @@ int jump_mixed(lb_handle_s* h, cudaStream_t s, const cplx* Z, cplx* Y, double al
     if (tc_split_planes(Z, n, n, n, 1, 0, m->sc + 2, m->Zp, np, (long long)np * np, 1, 0, (long long)np * np, s))
         return -1;
     k_mul2<<<1, 32, 0, s>>>(m->sc + 6, m->sc + 1, m->sc + 3); lb_note_launch();
-    // (1) P = L~_stack Z  -> h->P (d*np rows x n, complex128)
+    // scale of P from the bound, and the epilogue factor scale_P inv_L inv_Z
+    if (tc_bound_scale(m->sc + 11, m->sc + 8, m->sc + 6, m->sc + 4, m->sc + 5, m->sc + 10, s)) return -1;
+    // (1) P = L~_stack Z, written by the epilogue straight into the FP16 hi/lo planes that product (2)
+    // reads (d np rows of P_j, K-major as stored; padding rows and columns written as zeros)
     tc::Params p1{};
     p1.M = d * np;
-    p1.N = n;
+    p1.N = np;
     p1.nseg = 1;
     p1.seg[0] = tc::Seg{0, 1, 0, 0, 0, 0, 0, 0, 1, 0, np, tc::SIGN_NORMAL};
     p1.npairs = 3;
-    p1.out = h->P;
-    p1.ldo = n;
+    p1.out = nullptr;
+    p1.ldo = 0;
     p1.alpha = 1.0;
-    p1.scale = m->sc + 6;
+    p1.scale = m->sc + 10;
     p1.accumulate = 0;
     p1.err = err;
     p1.fmt = 0;
     p1.wave = -1;
+    p1.planes = m->Pp;
+    p1.plane_stride = (long long)d * np * np;
+    p1.plane_ld = np;
     prof_begin(h, s, 0);
-    if (tc_gemm_launch(m->maps, p1, d * np / tc::BM, (n + tc::BN - 1) / tc::BN, s)) return -1;
+    if (tc_gemm_launch(m->maps, p1, d * np / tc::BM, np / tc::BN, s)) return -1;
     prof_end(h, s, 0, 8.0 * d * (double)n * n * n);
-    // pack P_j (A operand of product (2), K-major rows as stored)
-    if (tc_maxabs(h->P, (long long)d * np * n, h->dpart, m->sc + 8, s)) return -1;
-    if (tc_pick_scale(m->sc + 8, m->sc + 4, m->sc + 5, s)) return -1;
-    if (tc_split_planes(h->P, n, np, n, 0, 0, m->sc + 4, m->Pp, np, (long long)d * np * np, d, (long long)np * n,
-                        (long long)np * np, s))
-        return -1;
     k_mul2<<<1, 32, 0, s>>>(m->sc + 7, m->sc + 5, m->sc + 1); lb_note_launch();
     // (2) Y = alpha sum_j P_j conj(L~_j)^T  : B rows are conj(L~_j) rows
     tc::Params p2{};
@@ -120,9 +128,12 @@ int jump_mixed(lb_handle_s* h, cudaStream_t s, const cplx* Z, cplx* Y, double al
     p2.err = err;
     p2.fmt = 0;
     p2.wave = -1;
+    p2.tri = herm;
     prof_begin(h, s, 0);
-    const int r = tc_gemm_launch(m->maps, p2, (n + tc::BM - 1) / tc::BM, (n + tc::BN - 1) / tc::BN, s);
-    prof_end(h, s, 0, 8.0 * d * (double)n * n * n);
+    int r = tc_gemm_launch(m->maps, p2, (n + tc::BM - 1) / tc::BM, (n + tc::BN - 1) / tc::BN, s);
+    if (!r && herm) r = mat_mirror_lower(Y, n, n, s);
+    // algorithmic work: the full product, or its Hermitian half (n (n + 1) / 2 entries)
+    prof_end(h, s, 0, (herm ? 4.0 * (n + 1) : 8.0 * n) * d * (double)n * n);
     return r;
 }
 

@@ -34,21 +34,30 @@ namespace {
 constexpr int LDS = KMAX + 2;        // leading dimension of the small column-major matrices
 constexpr int RKMAX = 16;            // largest recycled subspace
 
-// offsets (complex entries) of the small-matrix area h->gsm
-constexpr int OFF_G0 = 0;
-constexpr int OFF_A = OFF_G0 + LDS * KMAX;
-constexpr int OFF_F = OFF_A + LDS * KMAX;
-constexpr int OFF_RHS = OFF_F + LDS * KMAX;
+// offsets (complex entries) of the small-matrix area h->gsm (column-major small matrices)
+constexpr int OFF_G0 = 0;                              // G: rows x cols, ld LDS
+constexpr int OFF_A = OFF_G0 + LDS * KMAX;             // Householder work, ld LDS
+constexpr int OFF_F0 = OFF_A + LDS * KMAX;             // F: rows x cols, ld LDS
+constexpr int OFF_F2 = OFF_F0 + LDS * KMAX;            // F S (transformed), ld LDS
+constexpr int OFF_RHS = OFF_F2 + LDS * KMAX;
 constexpr int OFF_RHS0 = OFF_RHS + LDS;
 constexpr int OFF_Y = OFF_RHS0 + LDS;
 constexpr int OFF_G = OFF_Y + LDS;
-constexpr int OFF_M = OFF_G + LDS;
-constexpr int OFF_EV = OFF_M + KMAX * KMAX;
-constexpr int OFF_EVEC = OFF_EV + LDS;
-constexpr int OFF_GZ = OFF_EVEC + KMAX * KMAX;
-constexpr int OFF_BM = OFF_GZ + LDS * RKMAX;
+constexpr int OFF_GAM = OFF_G + LDS;                   // Gram matrix of [U^, V_p]: cols x cols, ld cols
+constexpr int OFF_GEV = OFF_GAM + KMAX * KMAX;         // its eigenvalues
+constexpr int OFF_GE = OFF_GEV + LDS;                  // its eigenvectors (Schur vectors), ld cols
+constexpr int OFF_S = OFF_GE + KMAX * KMAX;            // S = E_r Lambda_r^{-1/2}: cols x r, ld cols
+constexpr int OFF_M = OFF_S + KMAX * KMAX;             // M2: r x r, ld r
+constexpr int OFF_EV = OFF_M + KMAX * KMAX;            // eigenvalues of M2
+constexpr int OFF_EVEC = OFF_EV + LDS;                 // (eigenvectors of M2, unused)
+constexpr int OFF_YS = OFF_EVEC + KMAX * KMAX;         // Schur vectors of M2: r x r, ld r
+constexpr int OFF_Z = OFF_YS + KMAX * KMAX;            // Z = S Y_k: cols x knew, ld LDS
+constexpr int OFF_GZ = OFF_Z + LDS * RKMAX;            // G Z, then Q_s: rows x knew, ld LDS
+constexpr int OFF_ZR = OFF_GZ + LDS * RKMAX;           // Z R_s^{-1}: cols x knew, ld LDS
+constexpr int OFF_BM = OFF_ZR + LDS * RKMAX;
 constexpr int OFF_CU = OFF_BM + RKMAX * KMAX;
-constexpr int OFF_VU = OFF_CU + RKMAX * RKMAX;
+constexpr int OFF_UU = OFF_CU + RKMAX * RKMAX;
+constexpr int OFF_VU = OFF_UU + RKMAX * RKMAX;
 constexpr int OFF_C1 = OFF_VU + LDS * RKMAX;
 constexpr int OFF_C2 = OFF_C1 + LDS;
 constexpr int OFF_INV = OFF_C2 + LDS;
@@ -60,23 +69,76 @@ __device__ __forceinline__ double wsum(double v) {
     return v;
 }
 
-// One warp.  Builds the augmented relation matrix G = [[D, Bm], [0, Hbar]] (rows = kk + p + 1,
-// cols = kk + p; D = diag(dU)), F = [C, V_{p+1}]^H [U^, V_p] = [[CU, 0], [VU, I]] and the
-// right-hand side beta e_kk; Householder QR of G applied to F and the right-hand side;
-// y = argmin ||G y - rhs|| = R^{-1} (Q^H rhs); M = R^{-1} (Q^H F) whose eigenvalues are 1/theta
-// for the harmonic Ritz values theta of G^H G z = theta G^H F z; g = rhs - G y, res = ||g||.
-// Column-major, leading dimension LDS (M: ld cols).
+// Householder QR (one warp) of the rows x cols matrix A (ld LDS, in place: R on and above the
+// diagonal), the reflectors applied to the ncb columns of Bm (ld LDS) and to the vector b (nullable);
+// v: shared scratch of LDS entries
+__device__ void warp_house_qr(cplx* A, int rows, int cols, cplx* Bm, int ncb, cplx* b, cplx* v) {
+    const int lane = threadIdx.x;
+    for (int c = 0; c < cols && c < rows; ++c) {
+        double s2 = 0.0;
+        for (int i = c + lane; i < rows; i += 32) s2 += cabs2(A[c * LDS + i]);
+        s2 = wsum(s2);
+        const cplx x0 = A[c * LDS + c];
+        const double ax0 = hypot(x0.x, x0.y);
+        const double nx = sqrt(s2);
+        if (!(nx > 0.0)) continue;
+        const cplx ph = ax0 > 0.0 ? cscale(x0, 1.0 / ax0) : cmake(1.0, 0.0);
+        const cplx alpha = cscale(ph, -nx);
+        const cplx v0 = csub(x0, alpha);
+        const double vn2 = s2 - ax0 * ax0 + cabs2(v0);
+        __syncwarp();
+        for (int i = c + lane; i < rows; i += 32) v[i] = (i == c) ? v0 : A[c * LDS + i];
+        __syncwarp();
+        if (vn2 > 0.0) {
+            const double f = 2.0 / vn2;
+            for (int j = c + lane; j < cols + ncb; j += 32) {
+                cplx* col = j < cols ? A + j * LDS : Bm + (j - cols) * LDS;
+                cplx t = cmake(0, 0);
+                for (int i = c; i < rows; ++i) cfma(t, cconj(v[i]), col[i]);
+                t = cscale(t, f);
+                for (int i = c; i < rows; ++i) col[i] = csub(col[i], cmul(t, v[i]));
+            }
+            if (b && lane == 0) {
+                cplx t = cmake(0, 0);
+                for (int i = c; i < rows; ++i) cfma(t, cconj(v[i]), b[i]);
+                t = cscale(t, f);
+                for (int i = c; i < rows; ++i) b[i] = csub(b[i], cmul(t, v[i]));
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// X (cols x ncx, ld ldx) = R^{-1} Y (first cols rows of Y, ld LDS), R = upper(A[:cols, :cols]); lanes
+// take columns; a zero pivot gives 0
+__device__ void warp_back_subst(const cplx* A, int cols, const cplx* Y, int ncx, cplx* X, int ldx) {
+    for (int j = threadIdx.x; j < ncx; j += 32) {
+        for (int i = cols - 1; i >= 0; --i) {
+            cplx acc = Y[j * LDS + i];
+            for (int l = i + 1; l < cols; ++l) acc = csub(acc, cmul(A[l * LDS + i], X[j * ldx + l]));
+            const cplx d = A[i * LDS + i];
+            X[j * ldx + i] = (d.x == 0.0 && d.y == 0.0) ? cmake(0, 0) : cdiv(acc, d);
+        }
+    }
+}
+
+// One warp.  The augmented relation B [U^, V_p] = [C, V_{p+1}] G with G = [[D, Bm], [0, Hbar]]
+// (rows = kk + p + 1, cols = kk + p; D = diag(dU)); the least-squares update y = argmin ||G y - beta e_kk||
+// by Householder QR, g = beta e_kk - G y, res = ||g||; F = [C, V_{p+1}]^H [U^, V_p] = [[CU, 0], [VU, I]]
+// and the Gram matrix Gamma = [U^, V_p]^H [U^, V_p] = [[UU, VU_p^H], [VU_p, I]] for the harmonic Ritz
+// step.  Column-major, leading dimension LDS (Gamma: ld cols).
 __global__ void k_gcro_small(int kk, int p, const double* __restrict__ dU, const cplx* __restrict__ Bm,
                              const cplx* __restrict__ Hb, int ldh, const cplx* __restrict__ CU,
-                             const cplx* __restrict__ VU, double beta, cplx* gsm, double* res) {
+                             const cplx* __restrict__ UU, const cplx* __restrict__ VU, double beta, cplx* gsm,
+                             double* res) {
     cplx* G0 = gsm + OFF_G0;
     cplx* A = gsm + OFF_A;
-    cplx* F = gsm + OFF_F;
+    cplx* F = gsm + OFF_F0;
     cplx* rhs = gsm + OFF_RHS;
     cplx* rhs0 = gsm + OFF_RHS0;
     cplx* y = gsm + OFF_Y;
     cplx* g = gsm + OFF_G;
-    cplx* M = gsm + OFF_M;
+    cplx* Gam = gsm + OFF_GAM;
     __shared__ cplx v[LDS];
     const int lane = threadIdx.x;
     const int rows = kk + p + 1, cols = kk + p;
@@ -104,6 +166,14 @@ __global__ void k_gcro_small(int kk, int p, const double* __restrict__ dU, const
             A[j * LDS + i] = gv;
             F[j * LDS + i] = fv;
         }
+        for (int i = 0; i < cols; ++i) {
+            cplx gm;
+            if (i < kk && j < kk) gm = UU[j * RKMAX + i];
+            else if (i >= kk && j < kk) gm = VU[j * LDS + (i - kk)];
+            else if (i < kk && j >= kk) gm = cconj(VU[i * LDS + (j - kk)]);
+            else gm = cmake(i == j ? 1.0 : 0.0, 0.0);
+            Gam[j * cols + i] = gm;
+        }
     }
     for (int i = lane; i < rows; i += 32) {
         const cplx r = cmake(i == kk ? beta : 0.0, 0.0);
@@ -111,53 +181,13 @@ __global__ void k_gcro_small(int kk, int p, const double* __restrict__ dU, const
         rhs0[i] = r;
     }
     __syncwarp();
-    for (int c = 0; c < cols; ++c) {
-        double s2 = 0.0;
-        for (int i = c + lane; i < rows; i += 32) s2 += cabs2(A[c * LDS + i]);
-        s2 = wsum(s2);
-        const cplx x0 = A[c * LDS + c];
-        const double ax0 = hypot(x0.x, x0.y);
-        const double nx = sqrt(s2);
-        if (!(nx > 0.0)) continue;
-        const cplx ph = ax0 > 0.0 ? cscale(x0, 1.0 / ax0) : cmake(1.0, 0.0);
-        const cplx alpha = cscale(ph, -nx);
-        const cplx v0 = csub(x0, alpha);
-        const double vn2 = s2 - ax0 * ax0 + cabs2(v0);
-        for (int i = c + lane; i < rows; i += 32) v[i] = (i == c) ? v0 : A[c * LDS + i];
-        __syncwarp();
-        if (vn2 > 0.0) {
-            const double f = 2.0 / vn2;
-            for (int j = c + lane; j < cols; j += 32) {
-                cplx t = cmake(0, 0);
-                for (int i = c; i < rows; ++i) cfma(t, cconj(v[i]), A[j * LDS + i]);
-                t = cscale(t, f);
-                for (int i = c; i < rows; ++i) A[j * LDS + i] = csub(A[j * LDS + i], cmul(t, v[i]));
-            }
-            for (int j = lane; j < cols; j += 32) {
-                cplx t = cmake(0, 0);
-                for (int i = c; i < rows; ++i) cfma(t, cconj(v[i]), F[j * LDS + i]);
-                t = cscale(t, f);
-                for (int i = c; i < rows; ++i) F[j * LDS + i] = csub(F[j * LDS + i], cmul(t, v[i]));
-            }
-            if (lane == 0) {
-                cplx t = cmake(0, 0);
-                for (int i = c; i < rows; ++i) cfma(t, cconj(v[i]), rhs[i]);
-                t = cscale(t, f);
-                for (int i = c; i < rows; ++i) rhs[i] = csub(rhs[i], cmul(t, v[i]));
-            }
-        }
-        __syncwarp();
-    }
-    // back substitutions with R = upper(A[:cols, :cols]); a zero pivot (exact breakdown) gives 0
-    for (int j = lane; j <= cols; j += 32) {
-        // column j < cols of M, or (j == cols) the least-squares solution y
+    warp_house_qr(A, rows, cols, nullptr, 0, rhs, v);
+    if (lane == 0) {
         for (int i = cols - 1; i >= 0; --i) {
-            cplx acc = (j == cols) ? rhs[i] : F[j * LDS + i];
-            for (int l = i + 1; l < cols; ++l) acc = csub(acc, cmul(A[l * LDS + i], (j == cols) ? y[l] : M[j * cols + l]));
+            cplx acc = rhs[i];
+            for (int l = i + 1; l < cols; ++l) acc = csub(acc, cmul(A[l * LDS + i], y[l]));
             const cplx d = A[i * LDS + i];
-            const cplx val = (d.x == 0.0 && d.y == 0.0) ? cmake(0, 0) : cdiv(acc, d);
-            if (j == cols) y[i] = val;
-            else M[j * cols + i] = val;
+            y[i] = (d.x == 0.0 && d.y == 0.0) ? cmake(0, 0) : cdiv(acc, d);
         }
     }
     __syncwarp();
@@ -172,16 +202,145 @@ __global__ void k_gcro_small(int kk, int p, const double* __restrict__ dU, const
     if (lane == 0) res[0] = sqrt(r2);
 }
 
-// GZ = G0 Z for the knew leading eigenvectors Z (vector t contiguous, length cols)
-__global__ void k_gcro_gz(int rows, int cols, int knew, const cplx* gsm_in, cplx* gsm) {
-    const cplx* G0 = gsm_in + OFF_G0;
-    const cplx* Z = gsm_in + OFF_EVEC;
+// One warp.  From the eigenpairs (Lambda, E) of Gamma: S = E_r Lambda_r^{-1/2} over the eigenvalues above
+// 1e-10 of the largest, so that [U^, V_p] S is orthonormal; then the harmonic Ritz problem on that
+// basis, (G S)^H (G S) w = theta (G S)^H (F S) w, as M2 = R^{-1} Q^H (F S) with G S = Q R (eigenvalues
+// 1 / theta).  rdim[0] = r (as a double).
+__global__ void k_gcro_harm(int kk, int p, cplx* gsm, double* rdim) {
+    const cplx* G0 = gsm + OFF_G0;
+    const cplx* F0 = gsm + OFF_F0;
+    const cplx* lam = gsm + OFF_GEV;
+    const cplx* E = gsm + OFF_GE;
+    cplx* S = gsm + OFF_S;
+    cplx* A = gsm + OFF_A;
+    cplx* F2 = gsm + OFF_F2;
+    cplx* M = gsm + OFF_M;
+    __shared__ cplx v[LDS];
+    __shared__ int idx[KMAX];
+    __shared__ int rs;
+    const int lane = threadIdx.x;
+    const int rows = kk + p + 1, cols = kk + p;
+    if (lane == 0) {
+        double lmax = 0.0;
+        for (int i = 0; i < cols; ++i) lmax = fmax(lmax, lam[i].x);
+        int r = 0;
+        for (int i = 0; i < cols; ++i)
+            if (lam[i].x > 1e-10 * lmax) idx[r++] = i;
+        rs = r;
+        rdim[0] = (double)r;
+    }
+    __syncwarp();
+    const int r = rs;
+    for (int c = lane; c < r; c += 32) {
+        const double f = 1.0 / sqrt(lam[idx[c]].x);
+        for (int i = 0; i < cols; ++i) S[c * cols + i] = cscale(E[idx[c] * cols + i], f);
+    }
+    __syncwarp();
+    for (int c = lane; c < r; c += 32) {
+        for (int i = 0; i < rows; ++i) {
+            cplx a = cmake(0, 0), b = cmake(0, 0);
+            for (int j = 0; j < cols; ++j) {
+                cfma(a, G0[j * LDS + i], S[c * cols + j]);
+                cfma(b, F0[j * LDS + i], S[c * cols + j]);
+            }
+            A[c * LDS + i] = a;
+            F2[c * LDS + i] = b;
+        }
+    }
+    __syncwarp();
+    warp_house_qr(A, rows, r, F2, r, nullptr, v);
+    warp_back_subst(A, r, F2, r, M, r);
+}
+
+// One warp.  Z = S Y_k (Y: the first knew Schur vectors of M2, ld r), GZ = G Z, Householder QR
+// GZ = Q_s R_s with Q_s formed explicitly (rows x knew, at OFF_GZ), ZR = Z R_s^{-1}; ok[0] = 1 when the
+// pivots of R_s stay above 1e-12 of the largest (else the previous recycled pair is kept)
+__global__ void k_gcro_zupdate(int kk, int p, int r, int knew, cplx* gsm, double* ok) {
+    const cplx* G0 = gsm + OFF_G0;
+    const cplx* S = gsm + OFF_S;
+    const cplx* Y = gsm + OFF_YS;
+    cplx* Z = gsm + OFF_Z;
     cplx* GZ = gsm + OFF_GZ;
-    for (int e = threadIdx.x; e < rows * knew; e += blockDim.x) {
-        const int i = e % rows, t = e / rows;
-        cplx acc = cmake(0, 0);
-        for (int j = 0; j < cols; ++j) cfma(acc, G0[j * LDS + i], Z[t * cols + j]);
-        GZ[t * LDS + i] = acc;
+    cplx* ZR = gsm + OFF_ZR;
+    cplx* Q = gsm + OFF_F2;     // explicit Q_s (rows x knew)
+    __shared__ cplx v[LDS];
+    const int lane = threadIdx.x;
+    const int rows = kk + p + 1, cols = kk + p;
+    for (int t = lane; t < knew; t += 32) {
+        for (int i = 0; i < cols; ++i) {
+            cplx a = cmake(0, 0);
+            for (int c = 0; c < r; ++c) cfma(a, S[c * cols + i], Y[t * r + c]);
+            Z[t * LDS + i] = a;
+        }
+    }
+    __syncwarp();
+    for (int t = lane; t < knew; t += 32) {
+        for (int i = 0; i < rows; ++i) {
+            cplx a = cmake(0, 0);
+            for (int j = 0; j < cols; ++j) cfma(a, G0[j * LDS + i], Z[t * LDS + j]);
+            GZ[t * LDS + i] = a;
+        }
+        for (int i = 0; i < rows; ++i) Q[t * LDS + i] = cmake(i == t ? 1.0 : 0.0, 0.0);
+    }
+    __syncwarp();
+    // QR of GZ: keep the reflectors to form Q_s = H_0 ... H_{knew-1} [I; 0]
+    cplx* Vh = gsm + OFF_A;     // reflector c in column c (ld LDS), its squared norm in Vh[c * LDS + LDS - 1]
+    for (int c = 0; c < knew; ++c) {
+        double s2 = 0.0;
+        for (int i = c + lane; i < rows; i += 32) s2 += cabs2(GZ[c * LDS + i]);
+        s2 = wsum(s2);
+        const cplx x0 = GZ[c * LDS + c];
+        const double ax0 = hypot(x0.x, x0.y), nx = sqrt(s2);
+        const cplx ph = ax0 > 0.0 ? cscale(x0, 1.0 / ax0) : cmake(1.0, 0.0);
+        const cplx alpha = cscale(ph, -nx);
+        const cplx v0 = csub(x0, alpha);
+        const double vn2 = nx > 0.0 ? s2 - ax0 * ax0 + cabs2(v0) : 0.0;
+        __syncwarp();
+        for (int i = c + lane; i < rows; i += 32) v[i] = (i == c) ? v0 : GZ[c * LDS + i];
+        __syncwarp();
+        for (int i = lane; i < LDS - 1; i += 32) Vh[c * LDS + i] = (i >= c && i < rows) ? v[i] : cmake(0, 0);
+        if (lane == 0) Vh[c * LDS + LDS - 1] = cmake(vn2, 0.0);
+        if (vn2 > 0.0) {
+            const double f = 2.0 / vn2;
+            for (int j = c + lane; j < knew; j += 32) {
+                cplx t = cmake(0, 0);
+                for (int i = c; i < rows; ++i) cfma(t, cconj(v[i]), GZ[j * LDS + i]);
+                t = cscale(t, f);
+                for (int i = c; i < rows; ++i) GZ[j * LDS + i] = csub(GZ[j * LDS + i], cmul(t, v[i]));
+            }
+        }
+        __syncwarp();
+    }
+    for (int c = knew - 1; c >= 0; --c) {
+        const double vn2 = Vh[c * LDS + LDS - 1].x;
+        if (vn2 > 0.0) {
+            const double f = 2.0 / vn2;
+            for (int j = lane; j < knew; j += 32) {
+                cplx t = cmake(0, 0);
+                for (int i = c; i < rows; ++i) cfma(t, cconj(Vh[c * LDS + i]), Q[j * LDS + i]);
+                t = cscale(t, f);
+                for (int i = c; i < rows; ++i) Q[j * LDS + i] = csub(Q[j * LDS + i], cmul(t, Vh[c * LDS + i]));
+            }
+        }
+        __syncwarp();
+    }
+    // ZR = Z R_s^{-1}: row i of ZR solves x R_s = z_i (lanes take rows)
+    for (int i = lane; i < cols; i += 32) {
+        for (int t = 0; t < knew; ++t) {
+            cplx acc = Z[t * LDS + i];
+            for (int l = 0; l < t; ++l) acc = csub(acc, cmul(ZR[l * LDS + i], GZ[t * LDS + l]));
+            const cplx d = GZ[t * LDS + t];
+            ZR[t * LDS + i] = (d.x == 0.0 && d.y == 0.0) ? cmake(0, 0) : cdiv(acc, d);
+        }
+    }
+    if (lane == 0) {
+        double dmax = 0.0, dmin = INFINITY;
+        for (int t = 0; t < knew; ++t) {
+            const double a = hypot(GZ[t * LDS + t].x, GZ[t * LDS + t].y);
+            dmax = fmax(dmax, a);
+            dmin = fmin(dmin, a);
+        }
+        ok[0] = (knew > 0 && dmin > 1e-12 * dmax && isfinite(dmin)) ? 1.0 : 0.0;
     }
 }
 
@@ -347,13 +506,15 @@ int gcrodr_solve(lb_handle_s* h, cudaStream_t s, const cplx* b, cplx* delta, dou
         *steps += pd;
         // V[pd] (zero after a breakdown) completes V_{pd+1}
         cplx* CU = gsm + OFF_CU;
+        cplx* UU = gsm + OFF_UU;
         cplx* VU = gsm + OFF_VU;
         for (int t = 0; t < kk; ++t) {
             if (vec_dot_block(h->Crc, nn, kk, h->Urc + t * nn, nn, CU + t * RKMAX, h->part, 0, s)) return -1;
+            if (vec_dot_block(h->Urc, nn, kk, h->Urc + t * nn, nn, UU + t * RKMAX, h->part, 0, s)) return -1;
             if (vec_dot_block(h->V, nn, pd + 1, h->Urc + t * nn, nn, VU + t * LDS, h->part, 0, s)) return -1;
         }
-        k_gcro_small<<<1, 32, 0, s>>>(kk, pd, h->dU, Bm, h->hm, h->ldh, CU, VU, beta, gsm, res_d); lb_note_launch();
-        const int rows = kk + pd + 1, cols = kk + pd;
+        k_gcro_small<<<1, 32, 0, s>>>(kk, pd, h->dU, Bm, h->hm, h->ldh, CU, UU, VU, beta, gsm, res_d); lb_note_launch();
+        const int cols = kk + pd;
         const cplx* y = gsm + OFF_Y;
         const cplx* g = gsm + OFF_G;
         // delta += P (U^ y_U + V_p y_V)
@@ -373,54 +534,59 @@ int gcrodr_solve(lb_handle_s* h, cudaStream_t s, const cplx* b, cplx* delta, dou
         } else if (vec_gemv(r, h->V, nn, pd + 1, g, nn, 1.0, 0, s)) {
             return -1;
         }
-        // new recycled pair: harmonic Ritz vectors of smallest |theta| (largest |1/theta| of M)
-        const int knew = std::min(k, cols);
-        if (knew > 0) {
-            if (small_schur(gsm + OFF_M, cols, cols, 0, 1, knew, gsm + OFF_EV, gsm + OFF_EVEC, nullptr, nullptr,
+        // new recycled pair: harmonic Ritz vectors of smallest |theta| on an orthonormal basis of
+        // range([U^, V_p]) (its Gram matrix's well-conditioned eigenvectors: once a cycle has nearly
+        // converged, [U^, V_p] is numerically rank-deficient and its null directions would pass for
+        // spurious harmonic Ritz vectors), as Schur vectors of the selected values; C = [C, V] Q_s and
+        // U = [U^, V_p] Z R_s^{-1} from the small QR G Z = Q_s R_s, so B U = C holds by construction
+        if (k > 0 && cols > 0) {
+            if (small_schur(gsm + OFF_GAM, cols, cols, 0, 0, 0, gsm + OFF_GEV, gsm + OFF_EVEC, nullptr, gsm + OFF_GE,
                             h->dinfo, s))
                 return -1;
-            k_gcro_gz<<<1, 256, 0, s>>>(rows, cols, knew, gsm, gsm); lb_note_launch();
-            const cplx* Z = gsm + OFF_EVEC;
-            const cplx* GZ = gsm + OFF_GZ;
-            for (int t = 0; t < knew; ++t) {
-                cplx* ut = h->Unw + t * nn;
-                cplx* ct = h->Cnw + t * nn;
-                const cplx* zt = Z + (size_t)t * cols;
-                const cplx* gzt = GZ + (size_t)t * LDS;
-                if (kk > 0) {
-                    if (vec_gemv(ut, h->Urc, nn, kk, zt, nn, 1.0, 0, s)) return -1;
-                    if (vec_gemv(ut, h->V, nn, pd, zt + kk, nn, 1.0, 1, s)) return -1;
-                    if (vec_gemv(ct, h->Crc, nn, kk, gzt, nn, 1.0, 0, s)) return -1;
-                    if (vec_gemv(ct, h->V, nn, pd + 1, gzt + kk, nn, 1.0, 1, s)) return -1;
-                } else {
-                    if (vec_gemv(ut, h->V, nn, pd, zt, nn, 1.0, 0, s)) return -1;
-                    if (vec_gemv(ct, h->V, nn, pd + 1, gzt, nn, 1.0, 0, s)) return -1;
-                }
+            k_gcro_harm<<<1, 32, 0, s>>>(kk, pd, gsm, h->dscal + 13); lb_note_launch();
+            double rd[2];
+            if (read_doubles(s, h->dscal + 12, rd, 2)) return -1;
+            const int rdim = (int)rd[1];
+            const int knew = std::min(k, rdim);
+            double ok = 0.0;
+            if (knew > 0) {
+                if (small_schur(gsm + OFF_M, rdim, rdim, 0, 1, knew, gsm + OFF_EV, gsm + OFF_EVEC, nullptr,
+                                gsm + OFF_YS, h->dinfo, s))
+                    return -1;
+                k_gcro_zupdate<<<1, 32, 0, s>>>(kk, pd, rdim, knew, gsm, h->dscal + 15); lb_note_launch();
+                if (read_doubles(s, h->dscal + 15, &ok, 1)) return -1;
             }
-            // QR of C~ by Gram-Schmidt twice, the same column operations on Y: B u_t = c_t is kept
-            cplx* inv = gsm + OFF_INV;
-            double* dnew = h->dU + RKMAX;
-            for (int t = 0; t < knew; ++t) {
-                cplx* ut = h->Unw + t * nn;
-                cplx* ct = h->Cnw + t * nn;
-                for (int pass = 0; pass < 2 && t > 0; ++pass) {
-                    if (vec_dot_block(h->Cnw, nn, t, ct, nn, c1, h->part, 0, s)) return -1;
-                    if (vec_gemv(ct, h->Cnw, nn, t, c1, nn, -1.0, 1, s)) return -1;
-                    if (vec_gemv(ut, h->Unw, nn, t, c1, nn, -1.0, 1, s)) return -1;
+            if (ok > 0.5) {
+                const cplx* QS = gsm + OFF_F2;
+                const cplx* ZR = gsm + OFF_ZR;
+                cplx* inv = gsm + OFF_INV;
+                double* dnew = h->dU + RKMAX;
+                for (int t = 0; t < knew; ++t) {
+                    cplx* ut = h->Unw + t * nn;
+                    cplx* ct = h->Cnw + t * nn;
+                    const cplx* qt = QS + (size_t)t * LDS;
+                    const cplx* zt = ZR + (size_t)t * LDS;
+                    if (kk > 0) {
+                        if (vec_gemv(ct, h->Crc, nn, kk, qt, nn, 1.0, 0, s)) return -1;
+                        if (vec_gemv(ct, h->V, nn, pd + 1, qt + kk, nn, 1.0, 1, s)) return -1;
+                        if (vec_gemv(ut, h->Urc, nn, kk, zt, nn, 1.0, 0, s)) return -1;
+                        if (vec_gemv(ut, h->V, nn, pd, zt + kk, nn, 1.0, 1, s)) return -1;
+                    } else {
+                        if (vec_gemv(ct, h->V, nn, pd + 1, qt, nn, 1.0, 0, s)) return -1;
+                        if (vec_gemv(ut, h->V, nn, pd, zt, nn, 1.0, 0, s)) return -1;
+                    }
+                    // unit columns for U: u^_t = u_t / ||u_t||, B u^_t = dU_t c_t
+                    if (vec_norms(ut, nn, h->dpart, h->dscal + 2, s)) return -1;
+                    k_inv_norm<<<1, 32, 0, s>>>(h->dscal + 2, inv, dnew + t); lb_note_launch();
+                    if (vec_scale_dev(ut, nn, inv, s)) return -1;
                 }
-                if (vec_norms(ct, nn, h->dpart, h->dscal + 2, s)) return -1;
-                k_inv_norm<<<1, 32, 0, s>>>(h->dscal + 2, inv, nullptr); lb_note_launch();
-                if (vec_scale_dev(ct, nn, inv, s) || vec_scale_dev(ut, nn, inv, s)) return -1;
-                if (vec_norms(ut, nn, h->dpart, h->dscal + 2, s)) return -1;
-                k_inv_norm<<<1, 32, 0, s>>>(h->dscal + 2, inv, dnew + t); lb_note_launch();
-                if (vec_scale_dev(ut, nn, inv, s)) return -1;
+                std::swap(h->Urc, h->Unw);
+                std::swap(h->Crc, h->Cnw);
+                if (cudaMemcpyAsync(h->dU, dnew, knew * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+                    return -1;
+                h->rc_have = knew;
+                kk = knew;
             }
-            std::swap(h->Urc, h->Unw);
-            std::swap(h->Crc, h->Cnw);
-            if (cudaMemcpyAsync(h->dU, dnew, knew * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-                return -1;
-            h->rc_have = knew;
-            kk = knew;
         }
         double rr = 0.0;
         if (read_doubles(s, res_d, &rr, 1)) return -1;

@@ -392,6 +392,10 @@ extern "C" lb_status low_spectrum(lindblad_handle h, int k, double mu, double et
     cplx* evv = h->part + (size_t)2 * KMAX * KMAX + KMAX;
     int j0 = 0, restart = 0;
     double worst = INFINITY;
+    // mixed precision: the inner solves run on the tensor cores while the eigen-residual falls, then in
+    // FP64 (W recomputed in FP64), keeping the thick-restart basis: the FP64 cycles refine the pairs
+    int prec = o.precision;
+    double prev_worst = INFINITY;
     OpFn OP = [&](const cplx* b, cplx* x) {
         // x = (mu - L~_eta)^{-1} b by preconditioned GMRES, zero initial guess
         if (vec_scale_copy(xsol, b, nn, cmake(0, 0), s)) return -1;
@@ -400,8 +404,8 @@ extern "C" lb_status low_spectrum(lindblad_handle h, int k, double mu, double et
         bn = read_double(s, h->dscal + 1);
         int steps = 0;
         double res = 0.0;
-        if (gcrodr_solve(h, s, b, xsol, mu, eta, o.gmres_m, o.recycle_k, 50, o.inner_tol * bn, o.precision, &steps,
-                         &res, nullptr))
+        if (gcrodr_solve(h, s, b, xsol, mu, eta, o.gmres_m, o.recycle_k, 50, o.inner_tol * bn, prec, &steps, &res,
+                         nullptr))
             return -1;
         inf.gmres_steps += steps;
         inf.phi_applies += 1;
@@ -453,6 +457,13 @@ extern "C" lb_status low_spectrum(lindblad_handle h, int k, double mu, double et
         inf.restarts = restart + 1;
         inf.residual_max = worst;
         if (worst < o.tol) { st = LB_OK; break; }
+        if (prec == LB_PREC_FP64 && o.precision == LB_PREC_MIXED) inf.refine_steps += 1;
+        if (prec == LB_PREC_MIXED && (worst < 1e-6 || !(worst < 0.5 * prev_worst))) {
+            prec = LB_PREC_FP64;
+            st = precond_prepare(h, s, mu, eta, LB_PREC_FP64, 0);
+            if (st != LB_OK) return st;
+        }
+        prev_worst = std::min(prev_worst, worst);
         if (mm < m) { st = LB_NOT_CONVERGED; break; }   // invariant subspace smaller than m: cannot restart
         // thick restart: Zb[:p] <- Zb Zs[:, :p]; Zb[p] <- Zb[m]; H <- [T_pp; beta Zs[m-1, :p]]
         LB_CHECK_CUDA(cudaMemcpyAsync(Zs, Zh.data(), (size_t)mm * mm * sizeof(cplx), cudaMemcpyHostToDevice, s));

@@ -158,6 +158,8 @@ __global__ void __launch_bounds__(256, 1) k_tc_gemm(const __grid_constant__ Maps
         m0 = I * BM;
         n0 = J * BN;
     }
+    // Hermitian output: the CTAs of tiles strictly below the diagonal leave before any set-up
+    if (p.tri && m0 > n0) return;
     // K units (batch x BK block) of this CTA: all of them, or chunk blockIdx.y of ksplit (wavefront)
     const bool split = p.wave >= 0 && p.ksplit > 1;
     int u_lo = 0, u_hi = 0x7fffffff;
@@ -280,7 +282,28 @@ __global__ void __launch_bounds__(256, 1) k_tc_gemm(const __grid_constant__ Maps
             tmem_ld32(lane_addr + c, vr);
             tmem_ld32(lane_addr + BN + c, vi);
             tmem_ld_wait();
-            if (ok && r < p.M) {
+            if (ok && r < p.M && p.planes) {
+                // FP16 hi/lo planes of the scaled result (the split in FP32: the scale is a power of two)
+                const float fs = (float)sc;
+                __half* base = p.planes + (long long)r * p.plane_ld + n0 + c;
+#pragma unroll
+                for (int t0 = 0; t0 < 32; t0 += 8) {
+                    if (n0 + c + t0 >= p.N) break;
+                    __align__(16) __half hr[8], lr[8], hi_[8], li[8];
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) {
+                        const float re = __uint_as_float(vr[t0 + t]) * fs, im = __uint_as_float(vi[t0 + t]) * fs;
+                        hr[t] = __float2half_rn(re);
+                        lr[t] = __float2half_rn(re - __half2float(hr[t]));
+                        hi_[t] = __float2half_rn(im);
+                        li[t] = __float2half_rn(im - __half2float(hi_[t]));
+                    }
+                    *reinterpret_cast<uint4*>(base + t0) = *reinterpret_cast<const uint4*>(hr);
+                    *reinterpret_cast<uint4*>(base + p.plane_stride + t0) = *reinterpret_cast<const uint4*>(lr);
+                    *reinterpret_cast<uint4*>(base + 2 * p.plane_stride + t0) = *reinterpret_cast<const uint4*>(hi_);
+                    *reinterpret_cast<uint4*>(base + 3 * p.plane_stride + t0) = *reinterpret_cast<const uint4*>(li);
+                }
+            } else if (ok && r < p.M) {
                 cplx* orow = p.out + (long long)r * p.ldo;
 #pragma unroll
                 for (int t = 0; t < 32; ++t) {
@@ -415,6 +438,52 @@ __global__ void k_maxabs_final(const unsigned long long* __restrict__ part, int 
     if (threadIdx.x == 0) out[0] = __longlong_as_double((long long)m);
 }
 
+// per-block maxima of the row 1-norms sum_k (|Re| + |Im|), one warp per row
+__global__ void k_row_l1_part(const cplx* __restrict__ A, long long rows, int cols, long long ld, double* part) {
+    __shared__ double red[8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double m = 0.0;
+    for (long long r = (long long)blockIdx.x * 8 + warp; r < rows; r += (long long)gridDim.x * 8) {
+        double acc = 0.0;
+        for (int k = lane; k < cols; k += 32) {
+            const cplx v = A[r * ld + k];
+            acc += fabs(v.x) + fabs(v.y);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        m = fmax(m, acc);
+    }
+    if (lane == 0) red[warp] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < 8; ++q) m = fmax(m, red[q]);
+        part[blockIdx.x] = m;
+    }
+}
+
+__global__ void k_max_part_final(const double* part, int nblk, double* out) {
+    double m = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += 32) m = fmax(m, part[b]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) out[0] = m;
+}
+
+// |(A B)_rc| <= max_r ||A_r,:||_1 max |B| and |B_kc| <= sqrt(2) max(|Re B_kc|, |Im B_kc|)
+__global__ void k_bound_scale(const double* a, const double* b, const double* c, double* scale, double* inv,
+                              double* fac) {
+    if (threadIdx.x != 0) return;
+    const double m = a[0] * b[0] * 1.4142135623730951;
+    int e = 0;
+    if (m > 0.0 && isfinite(m)) {
+        frexp(m, &e);
+        e = 14 - e;
+    }
+    scale[0] = ldexp(1.0, e);
+    inv[0] = ldexp(1.0, -e);
+    fac[0] = scale[0] * c[0];
+}
+
 __global__ void k_pick_scale(const double* maxabs, double* scale, double* inv) {
     if (threadIdx.x != 0) return;
     const double m = maxabs[0];
@@ -498,6 +567,19 @@ int tc_maxabs(const cplx* X, long long len, double* part, double* out, cudaStrea
                                              reinterpret_cast<unsigned long long*>(part)); lb_note_launch();
     tc::k_maxabs_final<<<1, 32, 0, s>>>(reinterpret_cast<const unsigned long long*>(part), blocks, out);
     lb_note_launch();
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int tc_max_row_l1(const cplx* A, long long rows, int cols, long long ld, double* part, double* out, cudaStream_t s) {
+    constexpr int blocks = 592;
+    tc::k_row_l1_part<<<blocks, 256, 0, s>>>(A, rows, cols, ld, part); lb_note_launch();
+    tc::k_max_part_final<<<1, 32, 0, s>>>(part, blocks, out); lb_note_launch();
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int tc_bound_scale(const double* a, const double* b, const double* c, double* scale_dev, double* inv_dev,
+                   double* fac_dev, cudaStream_t s) {
+    tc::k_bound_scale<<<1, 32, 0, s>>>(a, b, c, scale_dev, inv_dev, fac_dev); lb_note_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

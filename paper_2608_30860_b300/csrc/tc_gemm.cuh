@@ -62,6 +62,16 @@ struct Params {
     // wavefront mode only: the K range of each block (both segments, in BK blocks) is split into
     // ksplit chunks, chunk = blockIdx.y; partial products are added to out with FP64 atomics
     int ksplit;
+    // 1: the output is Hermitian (M = N); tiles strictly below the diagonal exit at once and are
+    // mirrored by the caller
+    int tri;
+    // non-null: instead of complex128 `out`, the epilogue writes the result (times scale[0] and alpha) as
+    // the four FP16 planes [re_hi, re_lo, im_hi, im_lo] of the next product's operand: plane q at
+    // planes + q * plane_stride, row r at r * plane_ld; every row < M and column < N is written (zeros
+    // included), so the padding of the planes is kept zero
+    __half* planes;
+    long long plane_stride;
+    int plane_ld;
 };
 
 }  // namespace tc
@@ -81,4 +91,10 @@ int tc_split_planes_bf16(const cplx* X, long long ld_src, int rows, int cols, in
 // out[0] = max over the len complex entries of max(|re|, |im|); part: >= 592 doubles of scratch
 int tc_maxabs(const cplx* X, long long len, double* part, double* out, cudaStream_t s);
 // scale_dev[0] = 2^e with 2^e * maxabs <= 2^14 ; inv_dev[0] = 2^-e  (maxabs from tc_maxabs)
+// the largest row 1-norm sum_k (|Re A_rk| + |Im A_rk|) over the rows of A (rows x cols, ld), to out[0]
+int tc_max_row_l1(const cplx* A, long long rows, int cols, long long ld, double* part, double* out, cudaStream_t s);
+// scale_dev[0] = 2^e with 2^e * a[0] * b[0] * sqrt(2) <= 2^14 (a bound on the next product's entries),
+// inv_dev[0] = 2^-e, fac_dev[0] = scale * c[0] (c: the product of the operands' inverse scales)
+int tc_bound_scale(const double* a, const double* b, const double* c, double* scale_dev, double* inv_dev,
+                   double* fac_dev, cudaStream_t s);
 int tc_pick_scale(const double* maxabs_dev, double* scale_dev, double* inv_dev, cudaStream_t s);

@@ -367,6 +367,25 @@ int gauge_split(cplx* H, cplx* L, int n, int d, const cplx* c_dev, cudaStream_t 
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
+// R <- R + R^dag in place: one thread per pair i <= j (the pair is read before either is written)
+__global__ void k_add_adjoint(cplx* R, int n) {
+    const long long len = (long long)n * n;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / n), j = (int)(e % n);
+        if (i > j) continue;
+        const cplx a = R[e], b = R[(long long)j * n + i];
+        const cplx v = cadd(a, cconj(b));
+        R[e] = v;
+        if (i != j) R[(long long)j * n + i] = cconj(v);
+        else R[e] = cmake(v.x, 0.0);
+    }
+}
+
+int mat_add_adjoint(cplx* R, int n, cudaStream_t s) {
+    k_add_adjoint<<<grid_for((long long)n * n), RT, 0, s>>>(R, n); lb_note_launch();
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 int mat_eye(cplx* X, int n, cplx a, cudaStream_t s) {
     k_eye<<<grid_for((long long)n * n), RT, 0, s>>>(X, n, a); lb_note_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : -1;

@@ -23,6 +23,8 @@ int mat_hermitize(cplx* Y, const cplx* X, int n, cudaStream_t s);
 // out[0] = max |x_e|, out[1] = ||x||_2 ; part: 2 * DOT_BLOCKS doubles
 int vec_norms(const cplx* x, long long len, double* part, double* out, cudaStream_t s);
 int mat_eye(cplx* X, int n, cplx a, cudaStream_t s);
+// R <- R + R^dag (in place)
+int mat_add_adjoint(cplx* R, int n, cudaStream_t s);
 // gauge split in place: L_k += c_k I, then H += (1/2i) sum_k (c_k^* L_k - c_k L_k^dag) (c_dev: d complex)
 int gauge_split(cplx* H, cplx* L, int n, int d, const cplx* c_dev, cudaStream_t s);
 int mat_add_diag_dev(cplx* X, int n, const cplx* a, double scale, cudaStream_t s);

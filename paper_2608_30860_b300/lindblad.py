@@ -20,6 +20,7 @@ LB_PREC_FP64 = 0
 LB_PREC_MIXED = 1
 LB_APPLY_FORM_M = 1
 LB_APPLY_SCHUR = 2
+LB_APPLY_HERMITIAN = 4
 LB_ROUTE_SCHUR = 0
 LB_ROUTE_EIG = 1
 LB_ROUTE_AUTO = 2
@@ -171,10 +172,12 @@ def lindblad_setup(H: torch.Tensor, L: torch.Tensor, opts: LbOpts | None = None)
 
 
 def phi_apply(h: Handle, X: torch.Tensor, Y: torch.Tensor | None = None, form: str = "phi",
-              schur: bool = False, precision: int = LB_PREC_FP64) -> torch.Tensor:
-    """Y = Phi(X) = -K(S^{-1} X) (form='phi') or M(X) = -S^{-1}(K X) (form='M')."""
+              schur: bool = False, precision: int = LB_PREC_FP64, hermitian: bool = False) -> torch.Tensor:
+    """Y = Phi(X) = -K(S^{-1} X) (form='phi') or M(X) = -S^{-1}(K X) (form='M'); hermitian=True promises a
+    Hermitian X (upper-tile jump term, exactly Hermitian result)."""
     Y = torch.empty_like(X) if Y is None else Y
-    flags = (LB_APPLY_FORM_M if form.lower() == "m" else 0) | (LB_APPLY_SCHUR if schur else 0)
+    flags = ((LB_APPLY_FORM_M if form.lower() == "m" else 0) | (LB_APPLY_SCHUR if schur else 0)
+             | (LB_APPLY_HERMITIAN if hermitian else 0))
     st = load_library().phi_apply(h.ptr, _dev(X, (h.n, h.n)), _dev(Y, (h.n, h.n)), flags, precision, _stream())
     if st != 0:
         raise LindbladError(st, "phi_apply")
@@ -182,11 +185,11 @@ def phi_apply(h: Handle, X: torch.Tensor, Y: torch.Tensor | None = None, form: s
 
 
 def jump_apply(h: Handle, X: torch.Tensor, Y: torch.Tensor | None = None, schur: bool = False,
-               precision: int = LB_PREC_FP64) -> torch.Tensor:
+               precision: int = LB_PREC_FP64, hermitian: bool = False) -> torch.Tensor:
     """Y = K(X) = sum_j L_j X L_j^dag (Schur-coordinate L~_j with schur=True)."""
     Y = torch.empty_like(X) if Y is None else Y
-    st = load_library().jump_apply(h.ptr, _dev(X, (h.n, h.n)), _dev(Y, (h.n, h.n)), LB_APPLY_SCHUR if schur else 0,
-                                   precision, _stream())
+    flags = (LB_APPLY_SCHUR if schur else 0) | (LB_APPLY_HERMITIAN if hermitian else 0)
+    st = load_library().jump_apply(h.ptr, _dev(X, (h.n, h.n)), _dev(Y, (h.n, h.n)), flags, precision, _stream())
     if st != 0:
         raise LindbladError(st, "jump_apply")
     return Y

@@ -255,3 +255,22 @@ def test_schur_backward_error_gate(B):
     with pytest.raises(B.LindbladError) as e:
         _setup(B, H, Ls, schur_tol=0.1 * err)
     assert e.value.status == -6
+
+
+@pytest.mark.parametrize("n", [70, 131])
+def test_hermitian_flag_matches_general_path(B, n):
+    """LB_APPLY_HERMITIAN (upper-tile jump term + mirror) gives the general path's result on a Hermitian
+    input, to FP64 rounding, and an exactly Hermitian output; in both coordinate systems."""
+    H, Ls = gi.random_lindbladian(n, d=3, seed=n + 1)
+    h, _ = _setup(B, H, Ls)
+    X = _cuda(gi.random_hermitian(n, seed=4))
+    for schur in (False, True):
+        yg = B.phi_apply(h, X, schur=schur).cpu().numpy()
+        yh = B.phi_apply(h, X, schur=schur, hermitian=True).cpu().numpy()
+        assert _rel(yh, yg) < 1e-12
+        if schur:
+            assert np.abs(yh - yh.conj().T).max() == 0.0
+        kg = B.jump_apply(h, X, schur=schur).cpu().numpy()
+        kh = B.jump_apply(h, X, schur=schur, hermitian=True).cpu().numpy()
+        assert _rel(kh, kg) < 1e-13 and np.abs(kh - kh.conj().T).max() == 0.0
+    B.lindblad_destroy(h)

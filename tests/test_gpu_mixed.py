@@ -134,3 +134,20 @@ def test_refinement_cap_returns_the_running_best(B):
     # one refinement step from the low-precision Arnoldi state already lands well below its residual
     assert info["residual_max"] < 1e-9
     B.lindblad_destroy(h)
+
+
+@pytest.mark.parametrize("n", [200, 384])
+def test_hermitian_flag_tensor_core_jump_term(B, n):
+    """Upper-tile tcgen05 product (2) + mirror against the full product on a Hermitian input, and the
+    oracle's K(X)."""
+    H, Ls = gi.random_lindbladian(n, d=3, seed=n)
+    h = B.lindblad_setup(_cuda(H), _cuda(np.stack(Ls)))
+    X = gi.random_hermitian(n, seed=6)
+    ref = K.System(H, Ls).K(X)
+    kg = B.jump_apply(h, _cuda(X), precision=B.LB_PREC_MIXED).cpu().numpy()
+    kh = B.jump_apply(h, _cuda(X), precision=B.LB_PREC_MIXED, hermitian=True).cpu().numpy()
+    assert _rel(kh, ref) < TOL_MIXED and _rel(kh, kg) < TOL_MIXED
+    Xs = _cuda(X)
+    ys = B.phi_apply(h, Xs, schur=True, precision=B.LB_PREC_MIXED, hermitian=True).cpu().numpy()
+    assert np.abs(ys - ys.conj().T).max() == 0.0
+    B.lindblad_destroy(h)
