@@ -455,10 +455,11 @@ def implicit_euler_gmres(sysm: System, rho0, dt, steps, tol=1e-10, m=32, k_recyc
 
 # ----------------------------------------------------------------------------- shift-invert
 def low_spectrum_shift_invert(sysm: System, k=4, mu=0.0, eta=1.0, tol=1e-8, m=20, p=None,
-                              restarts=30, inner_tol=1e-12, seed=0):
+                              restarts=30, inner_tol=1e-12, seed=0, k_recycle=0, inner_m=30):
     """Alg. 5: Krylov-Schur shift-invert Arnoldi on OP = (mu - L~_eta)^{-1}.
 
-    OP(b) is a right-preconditioned GMRES solve (Precond(., mu, eta)).  Ritz
+    OP(b) is a right-preconditioned GMRES solve (Precond(., mu, eta)); with k_recycle > 0 the
+    recycled pair of GCRO-DR is threaded through every OP application (App. A.2).  Ritz
     values nu map back by lambda = mu - 1/nu; a thick restart keeps the p
     largest-|nu| Schur vectors.  Stops when max_k ||L v_k - lambda_k v_k||_max
     < tol on the raw (unnormalised, non-hermitised) Ritz vectors."""
@@ -470,8 +471,14 @@ def low_spectrum_shift_invert(sysm: System, k=4, mu=0.0, eta=1.0, tol=1e-8, m=20
     mv = lambda X: sysm.shifted_deflated(X, mu, eta)
     pc = lambda X: sysm.precond(X, mu, eta)
 
+    rec = [None]
+
     def OP(b):
-        return gmres_right(mv, pc, b, np.zeros_like(b), m=30, restarts=20,
+        if k_recycle > 0:
+            x, rec[0], _ = gcrodr(mv, pc, b, np.zeros_like(b), m=inner_m, k=k_recycle, recycle=rec[0],
+                                  atol=inner_tol * max(hs_norm(b), 1e-300), max_cycles=20)
+            return x
+        return gmres_right(mv, pc, b, np.zeros_like(b), m=inner_m, restarts=20,
                            atol=inner_tol * max(hs_norm(b), 1e-300))
 
     V = [v0 / hs_norm(v0)]

@@ -301,11 +301,13 @@ def test_tierb_thermal_closed_form_larger_n():
     assert np.abs(rho - ref).max() < 1e-11
 
 
-def test_tierb_shift_invert_matches_dense():
-    """Alg. 5 returns the k smallest-|lambda| nonzero eigenvalues of the dense L."""
+@pytest.mark.parametrize("k_recycle", [0, 6])
+def test_tierb_shift_invert_matches_dense(k_recycle):
+    """Alg. 5 returns the k smallest-|lambda| nonzero eigenvalues of the dense L (inner solves plain or
+    with the recycled pair threaded through every OP application)."""
     H, Ls = gi.random_lindbladian(7, d=3, seed=8)
     s = K.System(H, Ls)
-    lam, vecs, info = K.low_spectrum_shift_invert(s, k=4, tol=1e-10, m=16)
+    lam, vecs, info = K.low_spectrum_shift_invert(s, k=4, tol=1e-10, m=16, k_recycle=k_recycle)
     ref = D.low_spectrum(H, Ls, 4)
     for r in ref:
         assert np.min(np.abs(lam - r)) < 1e-8 * abs(r)
