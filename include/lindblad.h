@@ -133,7 +133,9 @@ size_t lindblad_workspace_bytes(int n, int d, const lb_opts* opts);
 /* Set-up, once per Lindbladian (Sec. 1.2 Eq. (3); App. A.1).
  *   H_dev : n x n Hermitian Hamiltonian (device, complex128, row-major)
  *   L_dev : d stacked n x n jump operators (device, d*n*n complex128)
- * Copies H and L into the workspace, forms G = -iH - 1/2 sum_j L_j^dag L_j with one
+ * Copies H and L into the workspace (with opts->gauge_c, replaced on the device by the gauge-shifted
+ * L~_j = L_j + c_j I and H~ = H + (1/2i) sum_j (c_j^* L~_j - c_j L~_j^dag), Remark "Non-uniqueness of
+ * the decomposition"; every later call then uses that split), forms G = -iH - 1/2 sum_j L_j^dag L_j with one
  * stacked GEMM, computes the Schur form G = Q T Q^dag (eigenvectors -> QR -> upper
  * triangle of Q^dag G Q), the Schur-coordinate jump operators L~_j = Q^dag L_j Q and the
  * case-1 test of Theorem 1.  With opts->route != LB_ROUTE_SCHUR it also keeps R = Q^dag U and
@@ -242,7 +244,8 @@ lb_status low_spectrum(lindblad_handle h, int k, double mu, double eta, void* ev
  * Outputs (device, complex128, row-major): w (n x n); gH (n x n, nullable) and gL (d x n x n,
  * nullable), the sensitivities of J = Tr(O rho) with dJ = Re<gH, dH> + sum_j Re<gL_j, dL_j>,
  * <A, B> = Tr(A^dag B):  gH = i (rho w - w rho),  gL_j = -Ws L_j rho + 1/2 L_j (Ws rho + rho Ws),
- * Ws = w + w^dag.  FP64 throughout.  Errors: LB_INVALID_ARG, LB_S_SINGULAR (case 1),
+ * Ws = w + w^dag.  With a gauge set at set-up, gH and gL are the sensitivities with respect to H~ and
+ * L~_j taken as independent inputs.  FP64 throughout.  Errors: LB_INVALID_ARG, LB_S_SINGULAR (case 1),
  * LB_NOT_CONVERGED (best w and sensitivities returned). */
 lb_status steady_state_adjoint(lindblad_handle h, const void* rho_dev, const void* O_dev, void* w_dev,
                                void* gH_dev, void* gL_dev, const lb_opts* opts, lb_info* info,

@@ -348,15 +348,24 @@ __device__ void cta_trisylv_c64(const float2* T, float2* X, int n, float2* tiles
                 const int a = alo + slot, b = d - a;
                 float ax = 0.f, ay = 0.f;
                 if (valid) {
-                    for (int r = a + 1 + t4; r < GT; r += 4) {
-                        const float2 m = sa[a * P + r], x = sc[r * P + b];
-                        ax += m.x * x.x - m.y * x.y;
-                        ay += m.x * x.y + m.y * x.x;
+                    // independent terms, fully unrolled and predicated so that the loads overlap
+#pragma unroll
+                    for (int q = 0; q < GT / 4; ++q) {
+                        const int r = a + 1 + t4 + 4 * q;
+                        if (r < GT) {
+                            const float2 m = sa[a * P + r], x = sc[r * P + b];
+                            ax += m.x * x.x - m.y * x.y;
+                            ay += m.x * x.y + m.y * x.x;
+                        }
                     }
-                    for (int r = b + 1 + t4; r < GT; r += 4) {
-                        const float2 x = sc[a * P + r], m = sb[b * P + r];
-                        ax += x.x * m.x + x.y * m.y;
-                        ay += x.y * m.x - x.x * m.y;
+#pragma unroll
+                    for (int q = 0; q < GT / 4; ++q) {
+                        const int r = b + 1 + t4 + 4 * q;
+                        if (r < GT) {
+                            const float2 x = sc[a * P + r], m = sb[b * P + r];
+                            ax += x.x * m.x + x.y * m.y;
+                            ay += x.y * m.x - x.x * m.y;
+                        }
                     }
                 }
                 ax += __shfl_xor_sync(0xffffffffu, ax, 1);

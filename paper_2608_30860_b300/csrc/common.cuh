@@ -56,7 +56,7 @@ struct ZGemmArgs {
                   // only the tiles on and above the diagonal are computed, the rest is mirrored
 };
 
-// C[i][j] = conj(C[j][i]) for i > j (n x n, leading dimension ld)
+// C[i][j] = conj(C[j][i]) for i > j and Im C[i][i] = 0 (n x n, leading dimension ld)
 int mat_mirror_lower(cplx* C, int n, long long ld, cudaStream_t s);
 
 // host launchers (defined in the .cu files)

@@ -91,7 +91,8 @@ __global__ void __launch_bounds__(256) zgemm_f64_kernel(ZGemmArgs a) {
     }
 }
 
-// C[i][j] = conj(C[j][i]) below the diagonal, 32 x 32 tiles through shared memory (coalesced both ways)
+// C[i][j] = conj(C[j][i]) below the diagonal and Im C[i][i] = 0 (the result is Hermitian), 32 x 32 tiles
+// through shared memory (coalesced both ways)
 __global__ void k_mirror_lower(cplx* C, int n, long long ld) {
     __shared__ cplx t[32][33];
     const int bi = blockIdx.y, bj = blockIdx.x;   // destination tile (bi, bj), bi >= bj
@@ -105,6 +106,7 @@ __global__ void k_mirror_lower(cplx* C, int n, long long ld) {
     for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
         const int r = bi * 32 + yy, c = bj * 32 + tx;
         if (r < n && c < n && r > c) C[(long long)r * ld + c] = cconj(t[tx][yy]);
+        if (r < n && r == c) C[(long long)r * ld + c].y = 0.0;   // a Hermitian diagonal is real
     }
 }
 

@@ -437,8 +437,8 @@ void recycle_forget(lb_handle_s* h) {
 
 // Solves (mu - L~_eta) delta = b in Schur coordinates (B = A P, P = Precond(., mu, eta)) from delta = 0
 // by GCRO-DR(m, k) with the handle's recycled pair (kept when it belongs to the same (mu, eta,
-// precision)).  Stops when the residual norm <= atol, after max_cycles cycles, or when a cycle
-// reduces it by less than 10 %.  Uses V / hm (basis), X[5] (r), X[6] (P v), X[7] (jump output).
+// precision)).  Stops when the residual norm <= atol, after max_cycles cycles, or when three cycles in
+// a row each reduce it by less than 10 %.  Uses V / hm (basis), X[5] (r), X[6] (P v), X[7] (jump output).
 int gcrodr_solve(lb_handle_s* h, cudaStream_t s, const cplx* b, cplx* delta, double mu, double eta, int m,
                  int kreq, int max_cycles, double atol, int precision, int* steps, double* final_res, int* cycles_out) {
     const long long nn = (long long)h->n * h->n;
@@ -480,7 +480,7 @@ int gcrodr_solve(lb_handle_s* h, cudaStream_t s, const cplx* b, cplx* delta, dou
     double nr[2];
     if (read_doubles(s, h->dscal, nr, 2)) return -1;
     double beta = nr[1], prev = INFINITY;
-    int cyc = 0;
+    int cyc = 0, poor = 0;
     for (; cyc < max_cycles && beta > atol; ++cyc) {
         const int p = m - kk;
         if (vec_scale_copy(h->V, r, nn, cmake(1.0 / beta, 0), s)) return -1;
@@ -592,7 +592,10 @@ int gcrodr_solve(lb_handle_s* h, cudaStream_t s, const cplx* b, cplx* delta, dou
         if (read_doubles(s, res_d, &rr, 1)) return -1;
         prev = beta;
         beta = rr;
-        if (beta > 0.9 * prev) { ++cyc; break; }
+        // stagnation: three cycles in a row that gain less than 10 % (a recycled solve often stalls
+        // for a cycle or two until the pair has captured the slow direction, then resumes)
+        poor = beta > 0.9 * prev ? poor + 1 : 0;
+        if (poor >= 3) { ++cyc; break; }
     }
     *final_res = beta;
     if (cycles_out) *cycles_out += cyc;

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <complex>
 #include <vector>
 
@@ -396,12 +397,14 @@ extern "C" lb_status low_spectrum(lindblad_handle h, int k, double mu, double et
     // FP64 (W recomputed in FP64), keeping the thick-restart basis: the FP64 cycles refine the pairs
     int prec = o.precision;
     double prev_worst = INFINITY;
+    const bool verbose = std::getenv("LB_VERBOSE") != nullptr;   // diagnostics on stderr, no effect on results
     OpFn OP = [&](const cplx* b, cplx* x) {
         // x = (mu - L~_eta)^{-1} b by preconditioned GMRES, zero initial guess
         if (vec_scale_copy(xsol, b, nn, cmake(0, 0), s)) return -1;
         double bn = 0.0;
         if (vec_norms(b, nn, h->dpart, h->dscal, s)) return -1;
         bn = read_double(s, h->dscal + 1);
+        if (!std::isfinite(bn)) return -1;
         int steps = 0;
         double res = 0.0;
         if (gcrodr_solve(h, s, b, xsol, mu, eta, o.gmres_m, o.recycle_k, 50, o.inner_tol * bn, prec, &steps, &res,
@@ -409,6 +412,7 @@ extern "C" lb_status low_spectrum(lindblad_handle h, int k, double mu, double et
             return -1;
         inf.gmres_steps += steps;
         inf.phi_applies += 1;
+        if (verbose) fprintf(stderr, "  OP %d: %d inner steps, relative residual %.2e\n", inf.phi_applies, steps, res / bn);
         return vec_scale_copy(x, xsol, nn, cmake(1, 0), s);
     };
     // small results must not be overwritten by the GMRES of the next OP call: part is used by
@@ -456,6 +460,10 @@ extern "C" lb_status low_spectrum(lindblad_handle h, int k, double mu, double et
         }
         inf.restarts = restart + 1;
         inf.residual_max = worst;
+        if (verbose)
+            fprintf(stderr, "low_spectrum: cycle %d size %d precision %d worst eigen-residual %.3e, lambda_1 = %.6e %+.6ei, "
+                            "inner steps so far %d\n",
+                    restart, mm, prec, worst, lam[0].x, lam[0].y, inf.gmres_steps);
         if (worst < o.tol) { st = LB_OK; break; }
         if (prec == LB_PREC_FP64 && o.precision == LB_PREC_MIXED) inf.refine_steps += 1;
         if (prec == LB_PREC_MIXED && (worst < 1e-6 || !(worst < 0.5 * prev_worst))) {

@@ -158,15 +158,25 @@ k_sylv_leaf128(const float2* __restrict__ Tf, const float2* __restrict__ Ttf, in
                 const int a = alo + slot, b = d - a;
                 f2 acc0 = fmk(0.f, 0.f), acc1 = fmk(0.f, 0.f);
                 if (valid) {
-                    for (int r = a + 1 + t4; r < SB; r += 4) {
-                        const f2 m = ga[a * SP + r], y = Xs[pr + r][qc + b];
-                        acc0.x += m.x * y.x - m.y * y.y;
-                        acc0.y += m.x * y.y + m.y * y.x;
+                    // the (at most 8) terms of each thread are independent: fully unrolled and predicated
+                    // so that their shared-memory loads overlap (this chain of steps sets the leaf's time)
+#pragma unroll
+                    for (int q = 0; q < SB / 4; ++q) {
+                        const int r = a + 1 + t4 + 4 * q;
+                        if (r < SB) {
+                            const f2 m = ga[a * SP + r], y = Xs[pr + r][qc + b];
+                            acc0.x += m.x * y.x - m.y * y.y;
+                            acc0.y += m.x * y.y + m.y * y.x;
+                        }
                     }
-                    for (int r = b + 1 + t4; r < SB; r += 4) {
-                        const f2 y = Xs[pr + a][qc + r], m = gb[b * SP + r];
-                        acc1.x += y.x * m.x + y.y * m.y;
-                        acc1.y += y.y * m.x - y.x * m.y;
+#pragma unroll
+                    for (int q = 0; q < SB / 4; ++q) {
+                        const int r = b + 1 + t4 + 4 * q;
+                        if (r < SB) {
+                            const f2 y = Xs[pr + a][qc + r], m = gb[b * SP + r];
+                            acc1.x += y.x * m.x + y.y * m.y;
+                            acc1.y += y.y * m.x - y.x * m.y;
+                        }
                     }
                 }
                 f2 sum = fmk(acc0.x + acc1.x, acc0.y + acc1.y);
