@@ -280,7 +280,8 @@ def gcrodr(matvec, precond, b, x0, m=32, k=8, recycle=None, atol=0.0, max_cycles
     k harmonic Ritz vectors of B on range([U D, V_p]) with the smallest harmonic Ritz values,
     i.e. G^H G z = theta G^H [C, V_{p+1}]^H [U D, V_p] z, become the new (U, C) through the small QR
     G Z = Q R (C = [C, V_{p+1}] Q, U = [U D, V_p] Z R^{-1}); the problem is posed on an orthonormal basis
-    of range([U D, V_p]) and the pair is kept when R is numerically singular.
+    of range([U D, V_p]); the pair is kept unchanged when R is ill-conditioned (pivots below 1e-6 of
+    the largest) or when the cycle met the tolerance.
     ``recycle`` = (U, C) of an earlier solve with the same operator (kept as is); the returned
     pair is to be passed to the next solve.  ``cycle_hook(x)`` returning True stops early."""
     x = np.array(x0, dtype=np.complex128)
@@ -368,7 +369,9 @@ def gcrodr(matvec, precond, b, x0, m=32, k=8, recycle=None, atol=0.0, max_cycles
         Z = S @ Ys[:, :min(sdim, kq)]
         Qs, Rs = np.linalg.qr(G @ Z)
         dg = np.abs(np.diag(Rs))
-        if dg.size and dg.min() > 1e-12 * dg.max():
+        # a cycle that met the tolerance keeps the pair: the end of a converged Krylov space is rounding
+        # noise, and each update multiplies the pair's relation error by ||R^{-1}||
+        if dg.size and dg.min() > 1e-6 * dg.max() and hs_norm(r) > atol:
             ZR = Z @ np.linalg.inv(Rs)
             C = [_combine(Vhat, Qs[:, t]) for t in range(Qs.shape[1])]
             U = [_combine(What, ZR[:, t]) for t in range(ZR.shape[1])]
