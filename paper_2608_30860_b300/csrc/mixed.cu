@@ -8,6 +8,8 @@
 // The L~_j planes are packed once at set-up; Z is packed per call with a power-of-two scale
 // (max |entry| -> 2^14); P's scale comes from the bound max_r ||L~_r,:||_1 sqrt(2) max|Z| (P is never
 // stored in FP64), and the epilogues undo the scales.
+#include <algorithm>
+
 #include "lb_internal.cuh"
 #include "tc_gemm.cuh"
 #include "vecops.cuh"
@@ -26,6 +28,8 @@ struct MixedState {
 // sc[10] the factor product (1)'s epilogue applies (scale_P inv_L inv_Z),
 // sc[11] max_{j,r} sum_k (|Re L~_j[r,k]| + |Im L~_j[r,k]|) (set-up)
 namespace {
+
+constexpr int KSPLIT2 = 4;   // CTAs per output tile of product (2)
 
 inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
@@ -129,7 +133,12 @@ int jump_mixed(lb_handle_s* h, cudaStream_t s, const cplx* Z, cplx* Y, double al
     p2.fmt = 0;
     p2.wave = -1;
     p2.tri = herm;
+    // the K loop of (2) runs over d n products: split it over KSPLIT2 CTAs per tile (whole jumps per
+    // chunk when KSPLIT2 divides d), partial sums added in FP64 -- each FP32 accumulation chain is
+    // KSPLIT2 times shorter, and small n fills the SMs
+    p2.ksplit = std::min(d, KSPLIT2);
     prof_begin(h, s, 0);
+    if (p2.ksplit > 1 && cudaMemsetAsync(Y, 0, (size_t)n * n * sizeof(cplx), s) != cudaSuccess) return -1;
     int r = tc_gemm_launch(m->maps, p2, (n + tc::BM - 1) / tc::BM, (n + tc::BN - 1) / tc::BN, s);
     if (!r && herm) r = mat_mirror_lower(Y, n, n, s);
     // algorithmic work: the full product, or its Hermitian half (n (n + 1) / 2 entries)

@@ -160,14 +160,16 @@ __global__ void __launch_bounds__(256, 1) k_tc_gemm(const __grid_constant__ Maps
     }
     // Hermitian output: the CTAs of tiles strictly below the diagonal leave before any set-up
     if (p.tri && m0 > n0) return;
-    // K units (batch x BK block) of this CTA: all of them, or chunk blockIdx.y of ksplit (wavefront)
-    const bool split = p.wave >= 0 && p.ksplit > 1;
+    // K units (batch x BK block) of this CTA: all of them, or chunk c of ksplit (c = blockIdx.y in
+    // wavefront mode, blockIdx.z otherwise); split partial products are added to out with FP64 atomics
+    const bool split = p.ksplit > 1 && !p.planes;
     int u_lo = 0, u_hi = 0x7fffffff;
     if (split) {
+        const int chunk = p.wave >= 0 ? (int)blockIdx.y : (int)blockIdx.z;
         int units = 0;
         for (int g = 0; g < p.nseg; ++g) units += seg_iters(cta_seg(p, g, I, J), 1);
-        u_lo = (int)((long long)units * blockIdx.y / p.ksplit);
-        u_hi = (int)((long long)units * (blockIdx.y + 1) / p.ksplit);
+        u_lo = (int)((long long)units * chunk / p.ksplit);
+        u_hi = (int)((long long)units * (chunk + 1) / p.ksplit);
     }
     int total_iters = 0;
     {
@@ -536,7 +538,8 @@ int tc_gemm_launch(const tc::Maps& maps, const tc::Params& p, int grid_m, int gr
     if (p.wave < 0)
         for (int g = 0; g < p.nseg; ++g)
             if (p.seg[g].nbatch < 1 || p.seg[g].klen < 1) return -1;
-    tc::k_tc_gemm<<<dim3(grid_m, grid_n), 256, tc::SMEM_BYTES, s>>>(maps, p); lb_note_launch();
+    const int gz = (p.wave < 0 && p.ksplit > 1 && !p.planes) ? p.ksplit : 1;
+    tc::k_tc_gemm<<<dim3(grid_m, grid_n, gz), 256, tc::SMEM_BYTES, s>>>(maps, p); lb_note_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

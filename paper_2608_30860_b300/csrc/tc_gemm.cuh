@@ -59,8 +59,10 @@ struct Params {
     // over K in [(I+1) BM, nb BM) and segment 1 over [(J+1) BN, nb BN)
     int wave;
     int nb;
-    // wavefront mode only: the K range of each block (both segments, in BK blocks) is split into
-    // ksplit chunks, chunk = blockIdx.y; partial products are added to out with FP64 atomics
+    // ksplit > 1: the K range of each output tile (all segments and batches, in BK blocks) is split
+    // into ksplit chunks run by separate CTAs (chunk = blockIdx.y in wavefront mode, blockIdx.z
+    // otherwise); partial products are added to out with FP64 atomics (out must hold the addend, e.g.
+    // zeros); not with the planes epilogue
     int ksplit;
     // 1: the output is Hermitian (M = N); tiles strictly below the diagonal exit at once and are
     // mirrored by the caller
