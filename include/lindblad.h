@@ -42,7 +42,9 @@ typedef enum {
                                   steady_state returns the pure state |psi><psi| of that eigenvector */
     LB_ILL_CONDITIONED = 3,    /* eigenbasis route refused by the cond(U) gate; Schur route used */
     LB_INVALID_ARG = -1,
-    LB_CUDA_ERROR = -2,
+    LB_CUDA_ERROR = -2,        /* a CUDA call failed, or a bounded wait of a tensor-core kernel gave up
+                                  during the call (every solver and apply entry point checks the
+                                  device error word before returning; the result is then not valid) */
     LB_ETA_EXCLUDED = -3,      /* eta * Tr R_mu^S(I) == 1: the Sherman-Morrison preconditioner of
                                   Eq. ShermanMorr / Alg. 2 is undefined */
     LB_WORKSPACE_TOO_SMALL = -4,
@@ -141,7 +143,8 @@ size_t lindblad_workspace_bytes(int n, int d, const lb_opts* opts);
  * case-1 test of Theorem 1.  With opts->route != LB_ROUTE_SCHUR it also keeps R = Q^dag U and
  * R^{-1} for the eigenbasis route and applies the cond(U) gate.  On success *out receives a handle.
  * Returns LB_OK, or LB_ILL_CONDITIONED (handle valid, Schur route in use) when LB_ROUTE_EIG was
- * requested and the gate refused it.  Errors: LB_INVALID_ARG (n < 2, d < 1, null pointers),
+ * requested and the gate refused it.  Errors: LB_INVALID_ARG (n < 2, d < 1, null pointers, a NaN or
+ * Inf entry in H or L_j -- checked on the device before any factorisation),
  * LB_WORKSPACE_TOO_SMALL, LB_SOLVER_ERROR (a factorisation failed, or the Schur backward error
  * exceeds opts->schur_tol; info->schur_backward_err then carries the measured value and no handle
  * is returned), LB_CUDA_ERROR.  info (nullable) receives set-up diagnostics. */
@@ -208,7 +211,7 @@ lb_status steady_state_gmres(lindblad_handle h, void* rho_dev, const lb_opts* op
  *   B_dev, X_dev : n x n device complex128 (must not alias).  X is written (no warm start).
  * The recycled subspace is kept in the handle for later solves at the same lam and precision.
  * Returns LB_OK, LB_NOT_CONVERGED (last iterate returned), LB_INVALID_ARG (lam <= 0, null or aliased
- * pointers), LB_NOT_IMPLEMENTED, LB_CUDA_ERROR. */
+ * pointers, a NaN or Inf entry in B), LB_NOT_IMPLEMENTED, LB_CUDA_ERROR. */
 lb_status resolvent_solve(lindblad_handle h, double lam, const void* B_dev, void* X_dev, const lb_opts* opts,
                           lb_info* info, void* stream);
 
@@ -221,7 +224,7 @@ lb_status resolvent_solve(lindblad_handle h, double lam, const void* B_dev, void
  *   traj_dev : nullable, nsteps stacked n x n device states after each step.
  * info: residual_max = the largest relative step residual, gmres_steps / phi_applies / restarts summed.
  * Returns LB_OK, LB_NOT_CONVERGED (a step missed the tolerance; the trajectory continues),
- * LB_INVALID_ARG (dt <= 0, nsteps < 1), LB_NOT_IMPLEMENTED, LB_CUDA_ERROR. */
+ * LB_INVALID_ARG (dt <= 0, nsteps < 1, a NaN or Inf entry in rho0), LB_NOT_IMPLEMENTED, LB_CUDA_ERROR. */
 lb_status implicit_euler(lindblad_handle h, const void* rho0_dev, double dt, int nsteps, void* rho_dev,
                          void* traj_dev, const lb_opts* opts, lb_info* info, void* stream);
 
@@ -315,6 +318,17 @@ lb_status lindbladian_apply_noalloc(const void* H_dev, const void* L_dev, int n,
 lb_status lb_set_profiling(lindblad_handle h, int enable);
 lb_status lb_kernel_stats(lindblad_handle h, int kernel, int* launches, double* total_ms,
                           double* algorithmic_flops);
+
+/* Test of the bounded waits (failure handling; no effect unless called).  Every mbarrier wait of
+ * the handle's tensor-core kernels gives up after wait_ms (0 < wait_ms <= 2000; 0 restores the
+ * default of 2000 ms), sets the handle's device error word and lets its warp fall through to the
+ * TMEM release, so the kernel ends and the context stays usable.  stall_iteration >= 0 makes the TMA
+ * producer of the NEXT jump-term product (1) issue no loads for that iteration of its K loop: the
+ * MMA issuer's wait for that stage runs out.  The call that contains that launch then returns
+ * LB_CUDA_ERROR (its result is not valid), and the error word is cleared.  stall_iteration = -1
+ * sets only the limit.  Errors: LB_INVALID_ARG (null handle, wait_ms outside [0, 2000],
+ * stall_iteration < -1). */
+lb_status lb_test_bounded_wait(lindblad_handle h, int stall_iteration, double wait_ms);
 
 /* Number of CUDA kernels this library has launched in this process so far (all handles). */
 long long lb_launch_count(void);

@@ -126,7 +126,7 @@ static int adjoint_residual(lb_handle_s* h, cudaStream_t s, const cplx* w, const
     return 0;
 }
 
-extern "C" lb_status steady_state_adjoint(lindblad_handle h, const void* rho_dev, const void* O_dev, void* w_dev,
+static lb_status steady_state_adjoint_body(lindblad_handle h, const void* rho_dev, const void* O_dev, void* w_dev,
                                           void* gH_dev, void* gL_dev, const lb_opts* opts, lb_info* info,
                                           void* stream) {
     if (!h || !rho_dev || !O_dev || !w_dev) return LB_INVALID_ARG;
@@ -206,4 +206,10 @@ extern "C" lb_status steady_state_adjoint(lindblad_handle h, const void* rho_dev
     inf.status = st;
     if (info) *info = inf;
     return st;
+}
+
+extern "C" lb_status steady_state_adjoint(lindblad_handle h, const void* rho_dev, const void* O_dev, void* w_dev,
+                                          void* gH_dev, void* gL_dev, const lb_opts* opts, lb_info* info,
+                                          void* stream) {
+    return device_error_guard(h, (cudaStream_t)stream, steady_state_adjoint_body(h, rho_dev, O_dev, w_dev, gH_dev, gL_dev, opts, info, stream));
 }

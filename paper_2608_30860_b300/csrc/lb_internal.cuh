@@ -53,6 +53,8 @@ struct lb_handle_s {
     cplx* E2 = nullptr;
     bool eig_active = false;           // FP64 Lyapunov solves use the eigenbasis route
     int arn_depth = 0;                 // nesting level of arnoldi_cycle (breakdown flag dinfo[12 + level])
+    unsigned long long tc_wait_ns = 0; // limit of the tensor-core kernels' mbarrier waits (0: 2 s)
+    int tc_stall = 0;                  // bounded-wait test: stall iteration + 1 of the next jump product (1)
     bool gauged = false;               // H, L hold the gauge-shifted H~, L~_j (lb_opts.gauge_c)
     double cond_eig = 0.0;
     bool ua_ready = false;
@@ -108,6 +110,7 @@ int arnoldi_cycle(lb_handle_s* h, cudaStream_t s, cplx* basis, cplx* hess, int j
 int hermitize_normalize(lb_handle_s* h, cudaStream_t s, const cplx* in, cplx* out, cplx* tmp);
 int residual_norms(lb_handle_s* h, cudaStream_t s, const cplx* rho, cplx* R, double* rmax, double* rfro);
 lb_status check_device_error(lb_handle_s* h, cudaStream_t s);
+lb_status device_error_guard(lb_handle_s* h, cudaStream_t s, lb_status st);
 lb_status steady_state_arnoldi(lb_handle_s* h, cudaStream_t s, const lb_opts& o, cplx* rho_out, lb_info* inf);
 
 // solvers.cu

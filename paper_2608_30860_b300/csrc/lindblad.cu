@@ -372,6 +372,14 @@ lb_status check_device_error(lb_handle_s* h, cudaStream_t s) {
     return LB_OK;
 }
 
+// the status of an entry point, or LB_CUDA_ERROR when a bounded wait of a tensor-core kernel gave up
+// during the call (the result is then not valid); the error word is cleared
+lb_status device_error_guard(lb_handle_s* h, cudaStream_t s, lb_status st) {
+    if (!h) return st;
+    const lb_status e = check_device_error(h, s);
+    return e != LB_OK ? e : st;
+}
+
 // ============================================================================ C ABI
 extern "C" {
 
@@ -449,6 +457,19 @@ lb_status lindblad_setup(const void* H_dev, const void* L_dev, int n, int d, voi
     if (cudaMemcpyAsync(h->H, H_dev, nn * sizeof(cplx), cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(h->L, L_dev, (size_t)d * nn * sizeof(cplx), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return fail(LB_CUDA_ERROR);
+    {
+        // NaN or Inf in H or L_j: refused before any factorisation (the sum of squares of the entries is
+        // finite exactly when every entry is finite and below ~1e154)
+        double fro[2] = {0.0, 0.0};
+        if (vec_norms(h->H, nn, h->dpart, h->dscal, s)) return fail(LB_CUDA_ERROR);
+        if (cudaMemcpyAsync(&fro[0], h->dscal + 1, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            return fail(LB_CUDA_ERROR);
+        if (vec_norms(h->L, (long long)d * nn, h->dpart, h->dscal, s)) return fail(LB_CUDA_ERROR);
+        if (cudaMemcpyAsync(&fro[1], h->dscal + 1, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return fail(LB_CUDA_ERROR);
+        if (!std::isfinite(fro[0]) || !std::isfinite(fro[1])) return fail(LB_INVALID_ARG);
+    }
     if (o.gauge_c) {
         // gauge of the split: the handle then holds (H~, L~_j); L is unchanged, S~ and K~ are not
         if (cudaMemcpyAsync(h->part, o.gauge_c, (size_t)d * sizeof(cplx), cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -626,6 +647,13 @@ lb_status lb_set_profiling(lindblad_handle h, int enable) {
     return LB_OK;
 }
 
+lb_status lb_test_bounded_wait(lindblad_handle h, int stall_iteration, double wait_ms) {
+    if (!h || !(wait_ms >= 0.0 && wait_ms <= 2000.0) || stall_iteration < -1) return LB_INVALID_ARG;
+    h->tc_wait_ns = (unsigned long long)(wait_ms * 1e6);
+    h->tc_stall = stall_iteration + 1;
+    return LB_OK;
+}
+
 lb_status lb_kernel_stats(lindblad_handle h, int kernel, int* launches, double* total_ms, double* flops) {
     if (!h || kernel < 0 || kernel > 1) return LB_INVALID_ARG;
     const auto& ev = h->prof_ev[kernel];
@@ -686,7 +714,7 @@ lb_status jump_apply(lindblad_handle h, const void* X_dev, void* Y_dev, int flag
     return jump_f64(h, s, h->Lt, X, Y, cmake(1, 0), cmake(0, 0), herm) ? LB_CUDA_ERROR : LB_OK;
 }
 
-lb_status resolvent_apply(lindblad_handle h, const void* Y_dev, void* X_dev, double lam, int precision,
+static lb_status resolvent_apply_body(lindblad_handle h, const void* Y_dev, void* X_dev, double lam, int precision,
                           void* stream) {
     if (!h || !Y_dev || !X_dev) return LB_INVALID_ARG;
     if (h->case1 && !(lam > 0.0)) return LB_S_SINGULAR;
@@ -701,12 +729,17 @@ lb_status resolvent_apply(lindblad_handle h, const void* Y_dev, void* X_dev, dou
     return LB_OK;
 }
 
+lb_status resolvent_apply(lindblad_handle h, const void* Y_dev, void* X_dev, double lam, int precision,
+                          void* stream) {
+    return device_error_guard(h, (cudaStream_t)stream, resolvent_apply_body(h, Y_dev, X_dev, lam, precision, stream));
+}
+
 lb_status lindbladian_apply(lindblad_handle h, const void* X_dev, void* R_dev, void* stream) {
     if (!h || !X_dev || !R_dev || X_dev == R_dev) return LB_INVALID_ARG;
     return lindbladian_f64(h, (cudaStream_t)stream, (const cplx*)X_dev, (cplx*)R_dev) ? LB_CUDA_ERROR : LB_OK;
 }
 
-lb_status steady_state(lindblad_handle h, void* rho_dev, const lb_opts* opts, lb_info* info, void* stream) {
+static lb_status steady_state_body(lindblad_handle h, void* rho_dev, const lb_opts* opts, lb_info* info, void* stream) {
     if (!h || !rho_dev) return LB_INVALID_ARG;
     lb_opts o = h->opts;
     if (opts) o = *opts;
@@ -741,6 +774,10 @@ lb_status steady_state(lindblad_handle h, void* rho_dev, const lb_opts* opts, lb
     inf.solve_ms = now_ms() - t0;
     if (info) *info = inf;
     return st;
+}
+
+lb_status steady_state(lindblad_handle h, void* rho_dev, const lb_opts* opts, lb_info* info, void* stream) {
+    return device_error_guard(h, (cudaStream_t)stream, steady_state_body(h, rho_dev, opts, info, stream));
 }
 
 }  // extern "C"

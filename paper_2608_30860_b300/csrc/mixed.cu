@@ -113,6 +113,9 @@ int jump_mixed(lb_handle_s* h, cudaStream_t s, const cplx* Z, cplx* Y, double al
     p1.planes = m->Pp;
     p1.plane_stride = (long long)d * np * np;
     p1.plane_ld = np;
+    p1.wait_ns = h->tc_wait_ns;
+    p1.test_stall = h->tc_stall;
+    h->tc_stall = 0;   // one launch only
     prof_begin(h, s, 0);
     if (tc_gemm_launch(m->maps, p1, d * np / tc::BM, np / tc::BN, s)) return -1;
     prof_end(h, s, 0, 8.0 * d * (double)n * n * n);
@@ -137,6 +140,7 @@ int jump_mixed(lb_handle_s* h, cudaStream_t s, const cplx* Z, cplx* Y, double al
     // chunk when KSPLIT2 divides d), partial sums added in FP64 -- each FP32 accumulation chain is
     // KSPLIT2 times shorter, and small n fills the SMs
     p2.ksplit = std::min(d, KSPLIT2);
+    p2.wait_ns = h->tc_wait_ns;
     prof_begin(h, s, 0);
     if (p2.ksplit > 1 && cudaMemsetAsync(Y, 0, (size_t)n * n * sizeof(cplx), s) != cudaSuccess) return -1;
     int r = tc_gemm_launch(m->maps, p2, (n + tc::BM - 1) / tc::BM, (n + tc::BN - 1) / tc::BN, s);

@@ -716,6 +716,15 @@ static int is_hermitian(lb_handle_s* h, cudaStream_t s, const cplx* B) {
     return v == 0.0 ? 1 : 0;
 }
 
+// every entry finite (the sum of squares is finite exactly when no entry is NaN or Inf and none is
+// above ~1e154)
+static bool all_finite(lb_handle_s* h, cudaStream_t s, const cplx* X, long long len) {
+    if (vec_norms(X, len, h->dpart, h->dscal, s)) return false;
+    double v[2];
+    if (read_doubles(s, h->dscal, v, 2)) return false;
+    return std::isfinite(v[1]);
+}
+
 static lb_status begin_solve(lb_handle_s* h, const lb_opts* opts, lb_opts& o) {
     o = h->opts;
     if (opts) o = *opts;
@@ -735,7 +744,7 @@ static void fill_common(lb_handle_s* h, lb_info& inf) {
 // ============================================================================ C ABI
 extern "C" {
 
-lb_status steady_state_gmres(lindblad_handle h, void* rho_dev, const lb_opts* opts, lb_info* info, void* stream) {
+static lb_status steady_state_gmres_body(lindblad_handle h, void* rho_dev, const lb_opts* opts, lb_info* info, void* stream) {
     if (!h || !rho_dev) return LB_INVALID_ARG;
     lb_opts o;
     lb_status st = begin_solve(h, opts, o);
@@ -788,7 +797,11 @@ lb_status steady_state_gmres(lindblad_handle h, void* rho_dev, const lb_opts* op
     return st;
 }
 
-lb_status resolvent_solve(lindblad_handle h, double lam, const void* B_dev, void* X_dev, const lb_opts* opts,
+lb_status steady_state_gmres(lindblad_handle h, void* rho_dev, const lb_opts* opts, lb_info* info, void* stream) {
+    return device_error_guard(h, (cudaStream_t)stream, steady_state_gmres_body(h, rho_dev, opts, info, stream));
+}
+
+static lb_status resolvent_solve_body(lindblad_handle h, double lam, const void* B_dev, void* X_dev, const lb_opts* opts,
                           lb_info* info, void* stream) {
     if (!h || !B_dev || !X_dev || B_dev == X_dev || !(lam > 0.0) || !std::isfinite(lam)) return LB_INVALID_ARG;
     lb_opts o;
@@ -801,6 +814,7 @@ lb_status resolvent_solve(lindblad_handle h, double lam, const void* B_dev, void
     fill_common(h, inf);
     const cplx* B = (const cplx*)B_dev;
     cplx* X = (cplx*)X_dev;
+    if (!all_finite(h, s, B, nn)) return LB_INVALID_ARG;
     const int herm = is_hermitian(h, s, B);
     if (herm < 0) return LB_CUDA_ERROR;
     if (vec_scale_copy(X, B, nn, cmake(0, 0), s)) return LB_CUDA_ERROR;
@@ -814,7 +828,12 @@ lb_status resolvent_solve(lindblad_handle h, double lam, const void* B_dev, void
     return st;
 }
 
-lb_status implicit_euler(lindblad_handle h, const void* rho0_dev, double dt, int nsteps, void* rho_dev,
+lb_status resolvent_solve(lindblad_handle h, double lam, const void* B_dev, void* X_dev, const lb_opts* opts,
+                          lb_info* info, void* stream) {
+    return device_error_guard(h, (cudaStream_t)stream, resolvent_solve_body(h, lam, B_dev, X_dev, opts, info, stream));
+}
+
+static lb_status implicit_euler_body(lindblad_handle h, const void* rho0_dev, double dt, int nsteps, void* rho_dev,
                          void* traj_dev, const lb_opts* opts, lb_info* info, void* stream) {
     if (!h || !rho0_dev || !rho_dev || rho0_dev == rho_dev || !(dt > 0.0) || !std::isfinite(dt) || nsteps < 1)
         return LB_INVALID_ARG;
@@ -831,6 +850,7 @@ lb_status implicit_euler(lindblad_handle h, const void* rho0_dev, double dt, int
     cplx* rho = (cplx*)rho_dev;
     cplx* b = h->bk0;
     if (cudaMemcpyAsync(rho, rho0_dev, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return LB_CUDA_ERROR;
+    if (!all_finite(h, s, rho, nn)) return LB_INVALID_ARG;
     const int herm = is_hermitian(h, s, rho);
     if (herm < 0) return LB_CUDA_ERROR;
     double worst = 0.0;
@@ -861,6 +881,11 @@ lb_status implicit_euler(lindblad_handle h, const void* rho0_dev, double dt, int
     inf.solve_ms = now_ms() - t0;
     if (info) *info = inf;
     return agg;
+}
+
+lb_status implicit_euler(lindblad_handle h, const void* rho0_dev, double dt, int nsteps, void* rho_dev,
+                         void* traj_dev, const lb_opts* opts, lb_info* info, void* stream) {
+    return device_error_guard(h, (cudaStream_t)stream, implicit_euler_body(h, rho0_dev, dt, nsteps, rho_dev, traj_dev, opts, info, stream));
 }
 
 }  // extern "C"

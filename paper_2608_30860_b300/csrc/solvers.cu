@@ -382,7 +382,7 @@ lb_status refine_steady_state(lb_handle_s* h, cudaStream_t s, const lb_opts& o, 
 }
 
 // ============================================================================ Alg. 5
-extern "C" lb_status low_spectrum(lindblad_handle h, int k, double mu, double eta, void* evals_host, void* evecs_dev,
+static lb_status low_spectrum_body(lindblad_handle h, int k, double mu, double eta, void* evals_host, void* evecs_dev,
                                   const lb_opts* opts, lb_info* info, void* stream) {
     if (!h || !evals_host) return LB_INVALID_ARG;
     lb_opts o = h->opts;
@@ -565,4 +565,9 @@ extern "C" lb_status low_spectrum(lindblad_handle h, int k, double mu, double et
     inf.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (info) *info = inf;
     return st;
+}
+
+extern "C" lb_status low_spectrum(lindblad_handle h, int k, double mu, double eta, void* evals_host, void* evecs_dev,
+                                  const lb_opts* opts, lb_info* info, void* stream) {
+    return device_error_guard(h, (cudaStream_t)stream, low_spectrum_body(h, k, mu, eta, evals_host, evecs_dev, opts, info, stream));
 }

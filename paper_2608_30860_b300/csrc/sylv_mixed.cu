@@ -300,6 +300,7 @@ int trisylv_mixed(lb_handle_s* h, cudaStream_t s, cplx* X, double shift) {
     p.scale = nullptr;
     p.accumulate = 1;
     p.err = h->dinfo + 8;
+    p.wait_ns = h->tc_wait_ns;
     p.fmt = 1;
     p.nb = nb;
     for (int w = 0; w <= 2 * nb - 2; ++w) {

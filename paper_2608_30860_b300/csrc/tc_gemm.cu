@@ -7,8 +7,8 @@
 //                     tcgen05.commit to the stage's "empty" barrier; warp 1 also owns TMEM;
 //   warps 4..7      : epilogue -- tcgen05.ld of the FP32 accumulators (each warp its 32-lane
 //                     quarter), scaling, FP64 complex store.
-// Three-stage ring.  Every mbarrier wait is bounded (~2 s of %globaltimer); a timeout sets the
-// error word and the roles fall through to the TMEM release.
+// Three-stage ring.  Every mbarrier wait is bounded (2 s of %globaltimer unless Params::wait_ns says
+// otherwise); a timeout sets the error word and the roles fall through to the TMEM release.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -42,12 +42,12 @@ __device__ __forceinline__ uint32_t mbar_try_wait(uint32_t bar, uint32_t parity)
         : "memory");
     return ok;
 }
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code) {
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code, uint64_t limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = gtimer();
     while (true) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (gtimer() - t0 > 2000000000ull) {
+        if (gtimer() - t0 > limit_ns) {
             atomicExch(err, code);
             return false;
         }
@@ -182,6 +182,7 @@ __global__ void __launch_bounds__(256, 1) k_tc_gemm(const __grid_constant__ Maps
         }
     }
     const uint32_t idesc_base = IDESC | ((uint32_t)p.fmt << 7) | ((uint32_t)p.fmt << 10);
+    const uint64_t limit = p.wait_ns ? p.wait_ns : 2000000000ull;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -218,9 +219,10 @@ __global__ void __launch_bounds__(256, 1) k_tc_gemm(const __grid_constant__ Maps
                     if (u < u_lo || u >= u_hi) continue;
                     const int kc = sg.k0 + kb * BK;
                     for (int pr = 0; pr < p.npairs; ++pr, ++it) {
+                        if (it + 1 == p.test_stall) continue;   // no loads: the stage never fills
                         const int s = it % STAGES;
                         const uint32_t ph = (it / STAGES) & 1;
-                        if (!mbar_wait(empty0 + 8 * s, ph ^ 1, p.err, 1)) { ok = false; break; }
+                        if (!mbar_wait(empty0 + 8 * s, ph ^ 1, p.err, 1, limit)) { ok = false; break; }
                         const int sa = (pr == 2) ? 1 : 0, sb = (pr == 1) ? 1 : 0;
                         const uint32_t st = sbase + s * STAGE_BYTES;
                         const uint32_t fb = full0 + 8 * s;
@@ -235,7 +237,7 @@ __global__ void __launch_bounds__(256, 1) k_tc_gemm(const __grid_constant__ Maps
         }
         // drain: the loads of the last (up to STAGES) issued stages must have landed
         for (int q = (it > STAGES ? it - STAGES : 0); q < it; ++q)
-            mbar_wait(full0 + 8 * (q % STAGES), (q / STAGES) & 1, p.err, 4);
+            mbar_wait(full0 + 8 * (q % STAGES), (q / STAGES) & 1, p.err, 4, limit);
     } else if (warp == 1 && lane == 0) {
         // ---------------------------------------------------------------- MMA issuer
         int it = 0, u = 0;
@@ -253,7 +255,7 @@ __global__ void __launch_bounds__(256, 1) k_tc_gemm(const __grid_constant__ Maps
             for (int q = 0; q < n_it; ++q, ++it) {
                 const int s = it % STAGES;
                 const uint32_t ph = (it / STAGES) & 1;
-                if (!mbar_wait(full0 + 8 * s, ph, p.err, 2)) { ok = false; break; }
+                if (!mbar_wait(full0 + 8 * s, ph, p.err, 2, limit)) { ok = false; break; }
                 fence_after();
                 const uint32_t st = sbase + s * STAGE_BYTES;
                 const uint64_t dAr = desc_sw128(st), dAi = desc_sw128(st + TILE_BYTES);
@@ -274,7 +276,7 @@ __global__ void __launch_bounds__(256, 1) k_tc_gemm(const __grid_constant__ Maps
     } else if (warp >= 4 && total_iters > 0) {
         // ---------------------------------------------------------------- epilogue
         const int wq = warp - 4;
-        const bool ok = mbar_wait(accf, 0, p.err, 3);
+        const bool ok = mbar_wait(accf, 0, p.err, 3, limit);
         fence_after();
         const int r = m0 + wq * 32 + lane;
         const double sc = p.alpha * (p.scale ? p.scale[0] : 1.0);

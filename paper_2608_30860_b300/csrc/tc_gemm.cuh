@@ -74,6 +74,11 @@ struct Params {
     __half* planes;
     long long plane_stride;
     int plane_ld;
+    // limit of every mbarrier wait in ns (0: 2 s); a wait that runs out sets *err and its role gives up
+    unsigned long long wait_ns;
+    // test of the bounded waits: s > 0 makes the TMA producer issue no loads for its iteration s - 1,
+    // so the MMA issuer's wait for that stage runs out (0: normal operation)
+    int test_stall;
 };
 
 }  // namespace tc

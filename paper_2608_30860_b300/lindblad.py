@@ -108,6 +108,8 @@ def load_library(path: str = LIB_PATH):
     lib.lb_set_profiling.restype = i
     lib.lb_kernel_stats.argtypes = [vp, i, P(i), P(d), P(d)]
     lib.lb_kernel_stats.restype = i
+    lib.lb_test_bounded_wait.argtypes = [vp, i, d]
+    lib.lb_test_bounded_wait.restype = i
     lib.lb_launch_count.argtypes = []
     lib.lb_launch_count.restype = ctypes.c_longlong
     lib.lb_status_string.argtypes = [i]
@@ -291,6 +293,15 @@ def lb_kernel_stats(h: Handle, kernel: int = 0):
     if st != 0:
         raise LindbladError(st, "lb_kernel_stats")
     return n.value, ms.value, fl.value
+
+
+def lb_test_bounded_wait(h: Handle, stall_iteration: int = -1, wait_ms: float = 0.0):
+    """Failure-handling test: the tensor-core kernels' mbarrier waits give up after wait_ms (0: 2 s); with
+    stall_iteration >= 0 the next jump-term product (1) issues no loads for that K iteration, so the call
+    that runs it returns LB_CUDA_ERROR."""
+    st = load_library().lb_test_bounded_wait(h.ptr, int(stall_iteration), float(wait_ms))
+    if st != 0:
+        raise LindbladError(st, "lb_test_bounded_wait")
 
 
 def lb_launch_count() -> int:
