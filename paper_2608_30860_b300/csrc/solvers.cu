@@ -526,6 +526,27 @@ static lb_status low_spectrum_body(lindblad_handle h, int k, double mu, double e
             prec = LB_PREC_FP64;
             st = precond_prepare(h, s, mu, eta, LB_PREC_FP64, 0);
             if (st != LB_OK) return st;
+            // explicit restart: a thick restart would keep the tensor-core OP images in the Krylov-Schur
+            // relation and bound every later Ritz pair at that precision; the FP64 cycles start from the
+            // sum of the k wanted Schur vectors (orthonormal, so no cancellation), which holds the
+            // wanted eigenvectors to the mixed accuracy
+            std::vector<cplx> y((size_t)mm, cmake(0, 0));
+            for (int j = 0; j < k; ++j)
+                for (int i = 0; i < mm; ++i) {
+                    y[i].x += Zh[(size_t)j * mm + i].x;
+                    y[i].y += Zh[(size_t)j * mm + i].y;
+                }
+            LB_CHECK_CUDA(cudaMemcpyAsync(h->small, y.data(), mm * sizeof(cplx), cudaMemcpyHostToDevice, s));
+            if (vec_gemv(h->V, Zb, nn, mm, h->small, nn, 1.0, 0, s)) return LB_CUDA_ERROR;
+            if (vec_norms(h->V, nn, h->dpart, h->dscal, s)) return LB_CUDA_ERROR;
+            const double z1 = read_double(s, h->dscal + 1);
+            if (!(z1 > 0.0) || !std::isfinite(z1)) return LB_CUDA_ERROR;
+            if (vec_scale_copy(Zb, h->V, nn, cmake(1.0 / z1, 0), s)) return LB_CUDA_ERROR;
+            LB_CHECK_CUDA(cudaMemsetAsync(h->hm2, 0, (size_t)(KMAX + 1) * (KMAX + 1) * sizeof(cplx), s));
+            j0 = 0;
+            prev_worst = INFINITY;
+            st = LB_NOT_CONVERGED;
+            continue;
         }
         prev_worst = std::min(prev_worst, worst);
         if (mm < m) { st = LB_NOT_CONVERGED; break; }   // invariant subspace smaller than m: cannot restart
