@@ -477,17 +477,19 @@ lb_status lindblad_setup(const void* H_dev, const void* L_dev, int n, int d, voi
             return fail(LB_CUDA_ERROR);
         h->gauged = true;
     }
-    // G = -iH - 1/2 sum_j L_j^dag L_j  (one stacked GEMM, K = d n)
-    if (vec_scale_copy(h->G, h->H, nn, cmake(0, -1), s)) return fail(LB_CUDA_ERROR);
+    // G = -iH - 1/2 sum_j L_j^dag L_j: the sum is Hermitian, so one stacked GEMM (K = d n) on its upper
+    // tiles plus the mirror, then the anti-Hermitian part -iH added
     {
         ZGemmArgs a{};
         a.M = n; a.N = n; a.K = d * n;
         a.A = h->L; a.lda = n; a.strideA = 0; a.opA = OP_C;
         a.B = h->L; a.ldb = n; a.strideB = 0; a.opB = OP_N;
-        a.C = h->G; a.ldc = n; a.strideC = 0;
-        a.alpha = cmake(-0.5, 0); a.beta = cmake(1, 0); a.batch = 1; a.reduce = 1;
+        a.C = h->X[0]; a.ldc = n; a.strideC = 0;
+        a.alpha = cmake(-0.5, 0); a.beta = cmake(0, 0); a.batch = 1; a.reduce = 1; a.herm = 1;
         if (zgemm_f64(a, s)) return fail(LB_CUDA_ERROR);
     }
+    if (vec_scale_copy(h->G, h->H, nn, cmake(0, -1), s)) return fail(LB_CUDA_ERROR);
+    if (vec_axpby(h->G, h->X[0], nn, cmake(1, 0), cmake(1, 0), s)) return fail(LB_CUDA_ERROR);
     // eigenvectors of G (column-major view of G^T storage is G), QR of them -> Schur vectors
     cplx* Acm = h->X[0];
     cplx* VR = h->X[1];
