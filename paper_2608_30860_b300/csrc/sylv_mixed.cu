@@ -84,6 +84,7 @@ k_sylv_leaf128(const float2* __restrict__ Tf, const float2* __restrict__ Ttf, in
     // side, each group synchronising on its own named barrier
     const int g = tid >> 7, lt = tid & 127;
     const int tx = lt & 31, ty = lt >> 5;            // rows ty + 4 i (i < 8) of the group's sub-block
+    const int slot = lt >> 2, t4 = lt & 3;           // leaf: 32 entries x 4 threads
     f2* ga = ta + g * 2 * SB * SP;                   // the group's two staging tiles
     f2* gb = ga + SB * SP;
     const int nsr = (br + SB - 1) / SB, nsc = (bc + SB - 1) / SB;
@@ -151,57 +152,53 @@ k_sylv_leaf128(const float2* __restrict__ Tf, const float2* __restrict__ Ttf, in
                                        ? f2ld(Tf + (long long)(c0 + qc + rr) * ldf + c0 + qc + tx) : fmk(0.f, 0.f);
             }
             group_sync(g);
-            // the 32 x 32 solve by anti-diagonals, one warp per sub-block (no CTA barrier inside the chain;
-            // __syncwarp orders the shared-memory writes of one step before the reads of the next).  Every
-            // entry (a, b) of anti-diagonal d has the same number of terms, (SB-1-a) + (SB-1-b) = 2 SB - 2 - d,
-            // so the combined A-/B-term list is split evenly over L lanes per entry, L the largest power of two
-            // with L x (entries on d) <= 32: the long late steps (few entries, many terms) use many lanes
-            if (lt < 32) {
-                for (int d = 2 * SB - 2; d >= 0; --d) {
-                    const int alo = max(0, d - (SB - 1));
-                    const int cnt = min(d, SB - 1) - alo + 1;
-                    const int lg = cnt > 16 ? 0 : cnt > 8 ? 1 : cnt > 4 ? 2 : cnt > 2 ? 3 : cnt > 1 ? 4 : 5;
-                    const int L = 1 << lg;
-                    const int ent = lt >> lg, e = lt & (L - 1);
-                    const bool valid = ent < cnt;
-                    const int a = alo + (valid ? ent : 0), b = d - a;
-                    const int nA = SB - 1 - a;             // A-terms: r = a+1 .. SB-1
-                    const int nt = 2 * (SB - 1) - d;       // A- plus B-terms of every entry on d
-                    // the divisor does not depend on the sums: formed first, off the chain
-                    const f2 da = ga[a * SP + a], db = gb[b * SP + b];
-                    const float dr = (da.x - sh) + (db.x - sh), di = da.y - db.y;   // A_aa + conj(B_bb)
-                    const float inv = 1.0f / (dr * dr + di * di);
-                    const f2 rhs = Xs[pr + a][qc + b];
-                    // term k: k < nA -> A_{a,r} Y_{r,b} (r = a+1+k); else Y_{a,r} conj(B_{b,r}) (r = b+1+k-nA)
-                    auto term = [&](int k, f2& acc) {
-                        const bool isA = k < nA;
-                        const int r = isA ? a + 1 + k : b + 1 + (k - nA);
-                        const f2 m = isA ? ga[a * SP + r] : gb[b * SP + r];
-                        const f2 y = isA ? Xs[pr + r][qc + b] : Xs[pr + a][qc + r];
-                        const float my = isA ? m.y : -m.y;
-                        acc.x += m.x * y.x - my * y.y;
-                        acc.y += m.x * y.y + my * y.x;
-                    };
-                    f2 acc0 = fmk(0.f, 0.f), acc1 = fmk(0.f, 0.f);
-                    int k = e;
-                    for (; k + L < nt; k += 2 * L) {
-                        term(k, acc0);
-                        term(k + L, acc1);
+            for (int d = 2 * SB - 2; d >= 0; --d) {
+                const int alo = max(0, d - (SB - 1)), cnt = min(d, SB - 1) - alo + 1;
+                const bool valid = slot < cnt;
+                const int a = alo + (valid ? slot : 0), b = d - a;
+                // the divisor and the right-hand side do not depend on the sums: read and formed first, off the
+                // chain of the step
+                const f2 da = ga[a * SP + a], db = gb[b * SP + b];
+                const float dr = (da.x - sh) + (db.x - sh), di = da.y - db.y;   // A_aa + conj(B_bb)
+                const float inv = 1.0f / (dr * dr + di * di);
+                const f2 rhs = Xs[pr + a][qc + b];
+                // two partial sums per kind (even / odd term) halve the dependent FMA chains
+                f2 acc0 = fmk(0.f, 0.f), acc1 = fmk(0.f, 0.f), acc2 = fmk(0.f, 0.f), acc3 = fmk(0.f, 0.f);
+                if (valid) {
+                    // the (at most 8) terms of each thread are independent: fully unrolled and predicated
+                    // so that their shared-memory loads overlap (this chain of steps sets the leaf's time)
+#pragma unroll
+                    for (int q = 0; q < SB / 4; ++q) {
+                        const int r = a + 1 + t4 + 4 * q;
+                        if (r < SB) {
+                            const f2 m = ga[a * SP + r], y = Xs[pr + r][qc + b];
+                            f2& acc = (q & 1) ? acc2 : acc0;
+                            acc.x += m.x * y.x - m.y * y.y;
+                            acc.y += m.x * y.y + m.y * y.x;
+                        }
                     }
-                    if (k < nt) term(k, acc0);
-                    f2 sum = fmk(acc0.x + acc1.x, acc0.y + acc1.y);
-                    for (int o = 1; o < L; o <<= 1) {
-                        sum.x += __shfl_xor_sync(0xffffffffu, sum.x, o);
-                        sum.y += __shfl_xor_sync(0xffffffffu, sum.y, o);
+#pragma unroll
+                    for (int q = 0; q < SB / 4; ++q) {
+                        const int r = b + 1 + t4 + 4 * q;
+                        if (r < SB) {
+                            const f2 y = Xs[pr + a][qc + r], m = gb[b * SP + r];
+                            f2& acc = (q & 1) ? acc3 : acc1;
+                            acc.x += y.x * m.x + y.y * m.y;
+                            acc.y += y.y * m.x - y.x * m.y;
+                        }
                     }
-                    if (valid && e == 0 && pr + a < br && qc + b < bc) {
-                        const f2 v = fmk(rhs.x - sum.x, rhs.y - sum.y);
-                        Xs[pr + a][qc + b] = fmk((v.x * dr + v.y * di) * inv, (v.y * dr - v.x * di) * inv);
-                    }
-                    __syncwarp();
                 }
+                f2 sum = fmk((acc0.x + acc2.x) + (acc1.x + acc3.x), (acc0.y + acc2.y) + (acc1.y + acc3.y));
+                sum.x += __shfl_xor_sync(0xffffffffu, sum.x, 1);
+                sum.y += __shfl_xor_sync(0xffffffffu, sum.y, 1);
+                sum.x += __shfl_xor_sync(0xffffffffu, sum.x, 2);
+                sum.y += __shfl_xor_sync(0xffffffffu, sum.y, 2);
+                if (valid && t4 == 0 && pr + a < br && qc + b < bc) {
+                    const f2 v = fmk(rhs.x - sum.x, rhs.y - sum.y);
+                    Xs[pr + a][qc + b] = fmk((v.x * dr + v.y * di) * inv, (v.y * dr - v.x * di) * inv);
+                }
+                group_sync(g);
             }
-            group_sync(g);
         }
         __syncthreads();
     }
