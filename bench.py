@@ -14,6 +14,7 @@ python bench.py --workload resolvent  # (lam - L) X = I/n, three shifts (Sec. 3.
 python bench.py --workload euler      # implicit Euler on the stiff n = 32 family (Sec. 4.3)
 python bench.py --workload gmres      # Alg. 3 steady state at n = 4096
 python bench.py --workload cat        # memory-buffer cat: steady state + 3 slowest modes across n
+python bench.py --workload spectrum   # k = 6 slowest modes of the 12-site TFIM by shift-invert Arnoldi (Alg. 5)
 Multi-GPU: replicas only (each rank runs its own copy of the workload; weak scaling).
 """
 from __future__ import annotations
@@ -211,8 +212,12 @@ def run_sweep(args, world, device):
     rho = torch.empty_like(Hd)
     ws = torch.empty(B.lindblad_batched_workspace_bytes(ns, d), dtype=torch.uint8, device=device)
     stream = torch.cuda.current_stream()
+    # tile shapes of the per-instance GEMMs from the library's autotuner (off the clock; a JSON cache is
+    # reused when it matches the device, d and the largest size)
+    tune = B.batched_tune(d, nmax=max(ns), cache=args.tile_cache) if args.tile_cache != "none" else None
+    tiles = tune["tiles"] if tune else None
     for _ in range(args.warmup):
-        B.steady_state_batched(ns, d, Hd, Ld, rho=rho, workspace=ws)
+        B.steady_state_batched(ns, d, Hd, Ld, rho=rho, workspace=ws, tiles=tiles)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -223,7 +228,7 @@ def run_sweep(args, world, device):
         torch.cuda.profiler.start()
         e0.record(stream)
         for _ in range(args.steps):
-            _, infos, st = B.steady_state_batched(ns, d, Hd, Ld, rho=rho, workspace=ws)
+            _, infos, st = B.steady_state_batched(ns, d, Hd, Ld, rho=rho, workspace=ws, tiles=tiles)
         e1.record(stream)
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
@@ -242,14 +247,14 @@ def run_sweep(args, world, device):
     for _ in range(args.steps):
         Hd.copy_(Hh, non_blocking=True)
         Ld.copy_(Lh, non_blocking=True)
-        B.steady_state_batched(ns, d, Hd, Ld, rho=rho, workspace=ws)
+        B.steady_state_batched(ns, d, Hd, Ld, rho=rho, workspace=ws, tiles=tiles)
         rho_h.copy_(rho, non_blocking=True)
     f1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = f0.elapsed_time(f1)
     return dict(ms=ms, e2e_ms=e2e_ms, clocks=clk.summary(), gpu_launches=gpu_launches, status=st,
                 worst=worst, applies=applies, anchors=anchors, flops32=flops32, params=params,
-                h2d=int(Hh.numel() + Lh.numel()) * 16, d2h=int(rho_h.numel()) * 16, ws_bytes=ws.numel())
+                h2d=int(Hh.numel() + Lh.numel()) * 16, d2h=int(rho_h.numel()) * 16, ws_bytes=ws.numel(), tune=tune)
 
 
 def sweep_line(args, r, world):
@@ -280,6 +285,12 @@ def sweep_line(args, r, world):
         "status": r["status"], "worst_residual_max": r["worst"],
         "phi_applies_mean": sum(r["applies"]) / count, "fp64_anchors_mean": sum(r["anchors"]) / count,
     }
+    if r.get("tune"):
+        t = r["tune"]
+        line["config"]["tiles"] = {b: t["shapes"][k] for b, k in zip(t["buckets"], t["tiles"])
+                                   if int(b.split("<=")[1]) - 16 < max(args.sweep_n[1], 16)}
+        line["config"]["tile_tuning"] = {"cached": t["cached"], "tune_s": round(t.get("tune_s", 0.0), 3),
+                                         "cache": args.tile_cache}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = sweep_cpu_baseline(r["params"])
     return line
@@ -548,6 +559,26 @@ def run_workload(args, device):
                         config={"workload": f"tfim{args.sites}_n{n}_d{len(Ls)}_alg3", "n": n, "d": len(Ls),
                                 "gmres_m": 32, "recycle_k": 8, "l2": "operands exceed L2"},
                         setup_s=round(setup_s, 2), solve=_solve_record(info, st, el), steps=1)
+        elif args.workload == "spectrum":
+            # the k = 6 slowest modes of the TFIM chain by shift-invert Arnoldi (Alg. 5, mu = 0, eta = 1) with
+            # recycled, right-preconditioned inner solves; eigen-residuals ||L v - lam v||_max / ||v||_max
+            H, Ls = gi.tfim(args.sites, J=1.0, h=1.0, gamma=0.3)
+            n = H.shape[0]
+            h, setup_s = _setup_case(B, torch, device, H, Ls, precision=prec)
+            B.lb_set_profiling(h, True)
+            t0 = time.perf_counter()
+            ev, _, info, st = B.low_spectrum(h, args.k, opts=B.default_opts(precision=prec, tol=args.spectrum_tol,
+                                                                          krylov_m=24, gmres_m=32, recycle_k=8))
+            el = time.perf_counter() - t0
+            line.update(metric=f"low spectrum (k={args.k}) by shift-invert Arnoldi, eigen-residual<={args.spectrum_tol:g}",
+                        value=el, unit="s", higher_is_better=False, ms_per_step=1000.0 * el, steps=1,
+                        config={"workload": f"tfim{args.sites}_n{n}_d{len(Ls)}_spectrum_k{args.k}", "n": n,
+                                "d": len(Ls), "k": args.k, "mu": 0.0, "eta": 1.0, "krylov_m": 24, "gmres_m": 32,
+                                "recycle_k": 8, "l2": "operands exceed L2" if n >= 2048 else "operands fit L2"},
+                        setup_s=round(setup_s, 2), status=st, residual_max=info["residual_max"],
+                        restarts=info["restarts"], op_applications=info["phi_applies"],
+                        inner_gmres_steps=info["gmres_steps"], fp64_cycles=info["refine_steps"],
+                        eigenvalues=[[float(x.real), float(x.imag)] for x in ev.numpy()])
         elif args.workload == "cat":
             # App. B memory-buffer cat: steady state (Alg. 4) and the 3 slowest modes (Alg. 5) across n
             per = {}
@@ -600,15 +631,21 @@ def main():
     ap.add_argument("--peaks", action="store_true",
                     help="only measure library GEMM peaks (FP64, FP32, TF32, complex64/128) and print them")
     ap.add_argument("--workload", default="tfim12",
-                    choices=["tfim12", "sweep", "resolvent", "euler", "gmres", "cat"],
+                    choices=["tfim12", "sweep", "resolvent", "euler", "gmres", "cat", "spectrum"],
                     help="tfim12: Phi applications + steady-state solves at n=4096 (default); sweep: the batched "
-                         "Kerr-cat sweep; resolvent / euler / gmres / cat: the GMRES-based solvers and the cat qubit")
+                         "Kerr-cat sweep; resolvent / euler / gmres / cat / spectrum: the GMRES-based solvers, the cat "
+                         "qubit and the TFIM low spectrum")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"], help="precision of the extra workloads")
     ap.add_argument("--n", type=int, default=1024, help="size of the resolvent workload")
     ap.add_argument("--cat-n", type=int, nargs="+", default=[256, 512, 1024], help="target sizes of the cat workload")
+    ap.add_argument("--k", type=int, default=6, help="eigenvalues of the spectrum workload")
+    ap.add_argument("--spectrum-tol", type=float, default=1e-8, help="eigen-residual tolerance of the spectrum workload")
     ap.add_argument("--sweep-count", type=int, default=SWEEP["count"],
                     help="instances of the sweep (1024: the benchmark; small values give profiler cases)")
     ap.add_argument("--sweep-n", type=int, nargs=2, default=SWEEP["n_range"], metavar=("NMIN", "NMAX"))
+    ap.add_argument("--tile-cache", default=os.path.join(os.path.expanduser("~"), ".cache", "lindblad_b300",
+                                                        "batched_tiles.json"),
+                    help="JSON cache of the batched engine's tile autotuner ('none': shape 0, no tuning)")
     ap.add_argument("--sites", type=int, default=12,
                     help="chain length (12: the n=4096 workload; smaller values give the small cases "
                          "used for profiler captures)")

@@ -98,7 +98,14 @@ typedef struct {
                              H~ = H + (1/2i) sum_j (c_j^* L~_j - c_j L~_j^dag); read by lindblad_setup only.
                              L is unchanged; the split S~ + K~ (and so Phi, the preconditioners and the
                              Schur form) is that of (H~, L~).  NULL = the split of Eq. (2) */
+    const int* batched_tiles; /* nullable host array of LB_TILE_BUCKETS entries: the complex64 GEMM tile
+                             shape (0 .. LB_TILE_SHAPES-1, see lindblad_batched_tune) that steady_state_batched
+                             uses for an instance of size n, indexed by min((n - 1) / 16, LB_TILE_BUCKETS - 1).
+                             NULL = shape 0 (32 x 32) for every size */
 } lb_opts;
+
+#define LB_TILE_BUCKETS 16
+#define LB_TILE_SHAPES 4
 
 /* Lyapunov route: Bartels-Stewart on the Schur form (App. A.1.1), or the eigenbasis divide of Alg. 1
  * (App. A.1.2) in Schur coordinates, X = R[(R^{-1} Y R^{-dag}) o D]R^dag with D_ij = 1/(s_i + s_j^* - lam)
@@ -287,6 +294,22 @@ size_t lindblad_batched_workspace_bytes(int count, const int* n, int d, const lb
 lb_status steady_state_batched(int count, const int* n, int d, const void* H_dev, const void* L_dev,
                                void* rho_dev, void* workspace, size_t ws_bytes, const lb_opts* opts,
                                lb_info* infos, void* stream);
+
+/* Tile autotuner of the batched engine (the per-instance complex64 GEMMs of the jump term).  For each of
+ * the LB_TILE_BUCKETS size buckets (n in (16 b, 16 (b + 1)], the last one open-ended; timed at
+ * n = min(16 (b + 1), nmax)) and each of the LB_TILE_SHAPES tile shapes -- 0: 32 x 32 output tile, K step
+ * 32, 4 x 1 register tile per thread; 1: 64 x 32, K 16, 4 x 2; 2: 64 x 64, K 16, 4 x 4; 3: 32 x 64, K 16,
+ * 2 x 4 -- it times the jump term y = -sum_j L_j Z L_j^dag exactly as the batched solve forms it, one
+ * synthetic instance per SM side by side (CUDA events on `stream`), and picks the fastest shape.
+ *   workspace : device memory of at least lindblad_batched_tune_workspace_bytes(d, nmax) bytes.
+ *   tiles_out : host array of LB_TILE_BUCKETS shapes, for lb_opts.batched_tiles.
+ *   us_out    : nullable host array of LB_TILE_BUCKETS x LB_TILE_SHAPES times (microseconds per jump
+ *               term per instance, bucket-major).
+ * Synchronises `stream`.  Errors: LB_INVALID_ARG (d < 1, nmax outside [2, 256], null workspace or
+ * tiles_out), LB_WORKSPACE_TOO_SMALL, LB_CUDA_ERROR.  0 bytes for invalid arguments. */
+size_t lindblad_batched_tune_workspace_bytes(int d, int nmax);
+lb_status lindblad_batched_tune(int d, int nmax, void* workspace, size_t workspace_bytes, int* tiles_out,
+                                float* us_out, void* stream);
 
 /* Largest n accepted by lindbladian_apply_noalloc (its scratch is sized for it). */
 #define LB_NOALLOC_NMAX 512

@@ -30,6 +30,7 @@ constexpr int GT = 32;    // CTA GEMM tile
 
 struct Inst {
     int n, status;
+    int tile;             // complex64 jump-term GEMM tile shape (tgemm_dispatch)
     long long in_off;     // offset (elements) of H / rho in the packed inputs; L at d * in_off
     long long off64;      // FP64 region (complex128 elements)
     long long off32;      // complex64 region
@@ -126,6 +127,94 @@ __device__ void cta_gemm(const C* A, int opA, const C* B, int opB, C* Cm, int n,
         }
     }
     __syncthreads();
+}
+
+// ------------------------------------------------------------------ tunable complex64 CTA GEMM
+// C = alpha sum_{s < nseg} A_s op(B_s): A_s = A + s a_seg (M x K row-major), B_s = B + s b_seg (opB 0: K x N
+// row-major; opB 2: N x K row-major, taken conjugate-transposed).  Output tile TM x TN per pass, K step KT,
+// the BT threads in a (TM/RM) x (TN/RN) grid with an RM x RN register tile each (rows tr + i TM/RM, columns
+// tc + j TN/RN: consecutive lanes read consecutive shared-memory columns).  sa: TM x (KT+1), sb: KT x (TN+1)
+// complex64 tiles.  The tile shape is the autotuner's choice per instance size.
+template <int TM, int TN, int KT, int RM, int RN>
+__device__ __noinline__ void tgemm_c64(const float2* __restrict__ A, long long a_seg, const float2* __restrict__ B,
+                                       long long b_seg, int opB, int nseg, float2* __restrict__ Cm, int M, int N, int K,
+                                       float alpha, float2* sa, float2* sb) {
+    constexpr int RG = TM / RM, CG = TN / RN;
+    static_assert(RG * CG == BT, "one register tile per thread");
+    const int t = threadIdx.x, tr = t / CG, tc = t % CG;
+    for (int r0 = 0; r0 < M; r0 += TM) {
+        for (int c0 = 0; c0 < N; c0 += TN) {
+            float2 acc[RM][RN];
+#pragma unroll
+            for (int i = 0; i < RM; ++i)
+#pragma unroll
+                for (int j = 0; j < RN; ++j) acc[i][j] = make_float2(0.f, 0.f);
+            for (int sg = 0; sg < nseg; ++sg) {
+                const float2* As = A + sg * a_seg;
+                const float2* Bs = B + sg * b_seg;
+                for (int k0 = 0; k0 < K; k0 += KT) {
+                    for (int e = t; e < TM * KT; e += BT) {
+                        const int rr = e / KT, kk = e % KT, gr = r0 + rr, gk = k0 + kk;
+                        sa[rr * (KT + 1) + kk] = (gr < M && gk < K) ? As[(long long)gr * K + gk] : make_float2(0.f, 0.f);
+                    }
+                    if (opB == 0) {
+                        for (int e = t; e < KT * TN; e += BT) {
+                            const int kk = e / TN, cc = e % TN, gk = k0 + kk, gc = c0 + cc;
+                            sb[kk * (TN + 1) + cc] = (gk < K && gc < N) ? Bs[(long long)gk * N + gc] : make_float2(0.f, 0.f);
+                        }
+                    } else {
+                        for (int e = t; e < KT * TN; e += BT) {
+                            const int cc = e / KT, kk = e % KT, gk = k0 + kk, gc = c0 + cc;
+                            float2 v = (gk < K && gc < N) ? Bs[(long long)gc * K + gk] : make_float2(0.f, 0.f);
+                            v.y = -v.y;
+                            sb[kk * (TN + 1) + cc] = v;
+                        }
+                    }
+                    __syncthreads();
+#pragma unroll 4
+                    for (int k = 0; k < KT; ++k) {
+                        float2 av[RM], bv[RN];
+#pragma unroll
+                        for (int i = 0; i < RM; ++i) av[i] = sa[(tr + RG * i) * (KT + 1) + k];
+#pragma unroll
+                        for (int j = 0; j < RN; ++j) bv[j] = sb[k * (TN + 1) + tc + CG * j];
+#pragma unroll
+                        for (int i = 0; i < RM; ++i)
+#pragma unroll
+                            for (int j = 0; j < RN; ++j) {
+                                acc[i][j].x += av[i].x * bv[j].x - av[i].y * bv[j].y;
+                                acc[i][j].y += av[i].x * bv[j].y + av[i].y * bv[j].x;
+                            }
+                    }
+                    __syncthreads();
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < RM; ++i)
+#pragma unroll
+                for (int j = 0; j < RN; ++j) {
+                    const int r = r0 + tr + RG * i, c = c0 + tc + CG * j;
+                    if (r < M && c < N) Cm[(long long)r * N + c] = make_float2(alpha * acc[i][j].x, alpha * acc[i][j].y);
+                }
+        }
+    }
+    __syncthreads();
+}
+
+// the tile shapes the autotuner chooses from: (TM, TN, KT, RM, RN)
+constexpr int NTILES = 4;
+__host__ __device__ inline const char* tile_name(int t) {
+    return t == 0 ? "32x32/k32/4x1" : t == 1 ? "64x32/k16/4x2" : t == 2 ? "64x64/k16/4x4" : "32x64/k16/2x4";
+}
+__device__ inline void tgemm_dispatch(int tile, const float2* A, long long a_seg, const float2* B, long long b_seg,
+                                      int opB, int nseg, float2* Cm, int M, int N, int K, float alpha, float2* sa,
+                                      float2* sb) {
+    switch (tile) {
+        case 1: tgemm_c64<64, 32, 16, 4, 2>(A, a_seg, B, b_seg, opB, nseg, Cm, M, N, K, alpha, sa, sb); break;
+        case 2: tgemm_c64<64, 64, 16, 4, 4>(A, a_seg, B, b_seg, opB, nseg, Cm, M, N, K, alpha, sa, sb); break;
+        case 3: tgemm_c64<32, 64, 16, 2, 4>(A, a_seg, B, b_seg, opB, nseg, Cm, M, N, K, alpha, sa, sb); break;
+        default: tgemm_c64<32, 32, 32, 4, 1>(A, a_seg, B, b_seg, opB, nseg, Cm, M, N, K, alpha, sa, sb); break;
+    }
 }
 
 // sum over the CTA of a double pair; red: >= 2 * (BT/32) doubles of shared memory
@@ -526,7 +615,7 @@ __device__ int cta_schur(cplx* A, cplx* Z, int n, cplx* hv, double* red, cplx* s
 constexpr int PK = 6;    // Ritz values nearest 1 carried across a restart (the first is the iterate)
 
 struct View {
-    int n, d;
+    int n, d, tile;
     cplx *G, *Q, *T, *Lt, *S1, *S2, *S3, *S4, *S5, *S6, *hv;   // FP64
     float2 *Tf, *Ltf, *V, *Wa, *Ub, *Z1, *Pf;                 // complex64
 };
@@ -542,6 +631,7 @@ __device__ View make_view(const Inst& in, int d, cplx* a64, float2* a32) {
     const long long nn = (long long)n * n;
     v.n = n;
     v.d = d;
+    v.tile = in.tile;
     cplx* p = a64 + in.off64;
     v.G = p; p += nn;
     v.Q = p; p += nn;
@@ -587,12 +677,12 @@ struct Shared {
 // y = alpha * sum_j L~_j Z L~_j^dag  (complex64, Pf scratch)
 __device__ void jump32(const View& v, const float2* Zin, float2* y, float alpha, Shared& sm) {
     const long long nn = (long long)v.n * v.n;
-    for (int j = 0; j < v.d; ++j)
-        cta_gemm(v.Ltf + j * nn, 0, Zin, 0, v.Pf + j * nn, v.n, make_float2(1.f, 0.f), make_float2(0.f, 0.f), 0,
-                 reinterpret_cast<float2*>(sm.ga), reinterpret_cast<float2*>(sm.gb));
-    for (int j = 0; j < v.d; ++j)
-        cta_gemm(v.Pf + j * nn, 0, v.Ltf + j * nn, 2, y, v.n, make_float2(alpha, 0.f), make_float2(1.f, 0.f), j > 0,
-                 reinterpret_cast<float2*>(sm.ga), reinterpret_cast<float2*>(sm.gb));
+    float2* sa = reinterpret_cast<float2*>(sm.ga);
+    float2* sb = reinterpret_cast<float2*>(sm.gb);
+    // (1) [P_1; ..; P_d] = [L~_1; ..; L~_d] Z  (one stacked product, M = d n)
+    tgemm_dispatch(v.tile, v.Ltf, 0, Zin, 0, 0, 1, v.Pf, v.d * v.n, v.n, v.n, 1.f, sa, sb);
+    // (2) y = alpha sum_j P_j L~_j^dag  (the sum over j inside one accumulation)
+    tgemm_dispatch(v.tile, v.Pf, nn, v.Ltf, nn, 2, v.d, y, v.n, v.n, v.n, alpha, sa, sb);
 }
 
 // w = Phi(x) = -K~(S~^{-1} x) in complex64 (Z1 scratch)
@@ -1087,7 +1177,7 @@ struct Plan {
     size_t bytes = 0, off_inst = 0, off_order = 0, off_info = 0, off_queue = 0, off64 = 0, off32 = 0;
 };
 
-bool make_plan(int count, const int* n, int d, Plan& p) {
+bool make_plan(int count, const int* n, int d, Plan& p, const int* tiles = nullptr) {
     p.insts.resize(count);
     long long in_off = 0;
     for (int i = 0; i < count; ++i) {
@@ -1095,6 +1185,8 @@ bool make_plan(int count, const int* n, int d, Plan& p) {
         Inst& in = p.insts[i];
         in.n = n[i];
         in.status = 0;
+        in.tile = tiles ? tiles[std::min((n[i] - 1) / 16, LB_TILE_BUCKETS - 1)] : 0;
+        if (in.tile < 0 || in.tile >= NTILES) return false;
         in.in_off = in_off;
         in.off64 = p.n64;
         in.off32 = p.n32;
@@ -1117,7 +1209,98 @@ bool make_plan(int count, const int* n, int d, Plan& p) {
     return true;
 }
 
+// ------------------------------------------------------------------ tile autotuner
+// Deterministic complex64 operands for the tuner (values in [-1, 1], no randomness needed for timing).
+__global__ void k_tune_fill(float2* buf, long long len) {
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += (long long)gridDim.x * blockDim.x)
+        buf[e] = make_float2(__sinf(0.37f * (float)(e % 9973)), __cosf(0.11f * (float)(e % 7919)));
+}
+
+// One CTA per synthetic instance of size n: reps complex64 jump terms y = -sum_j L_j (Z) L_j^dag with tile
+// shape `tile`, exactly as jump32 forms them.  Slice of CTA b: L (d n^2), Z (n^2), P (d n^2), y (n^2).
+__global__ void __launch_bounds__(BT, 1) k_tune_jump(int tile, int n, int d, float2* buf, int reps) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    Shared& sm = *reinterpret_cast<Shared*>(smraw);
+    const long long nn = (long long)n * n;
+    float2* L = buf + (long long)blockIdx.x * (2 * d + 2) * nn;
+    float2* Z = L + d * nn;
+    float2* P = Z + nn;
+    float2* y = P + d * nn;
+    float2* sa = reinterpret_cast<float2*>(sm.ga);
+    float2* sb = reinterpret_cast<float2*>(sm.gb);
+    for (int r = 0; r < reps; ++r) {
+        tgemm_dispatch(tile, L, 0, Z, 0, 0, 1, P, d * n, n, n, 1.f, sa, sb);
+        tgemm_dispatch(tile, P, nn, L, nn, 2, d, y, n, n, n, -1.f, sa, sb);
+    }
+}
+
 }  // namespace bt
+
+namespace {
+int tune_instances() {
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    return nsm;
+}
+}  // namespace
+
+extern "C" size_t lindblad_batched_tune_workspace_bytes(int d, int nmax) {
+    if (d < 1 || nmax < 2 || nmax > 256) return 0;
+    return (size_t)tune_instances() * (2 * d + 2) * (size_t)nmax * nmax * sizeof(float2);
+}
+
+extern "C" lb_status lindblad_batched_tune(int d, int nmax, void* workspace, size_t ws_bytes, int* tiles_out,
+                                           float* us_out, void* stream) {
+    if (d < 1 || nmax < 2 || nmax > 256 || !workspace || !tiles_out) return LB_INVALID_ARG;
+    const size_t need = lindblad_batched_tune_workspace_bytes(d, nmax);
+    if (ws_bytes < need) return LB_WORKSPACE_TOO_SMALL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int smem = (int)sizeof(bt::Shared);
+    if (lb_smem_attr((const void*)bt::k_tune_jump, smem)) return LB_CUDA_ERROR;
+    const int ninst = tune_instances();
+    float2* buf = static_cast<float2*>(workspace);
+    bt::k_tune_fill<<<1184, 256, 0, s>>>(buf, (long long)(need / sizeof(float2)));
+    lb_note_launch();
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    LB_CHECK_CUDA(cudaEventCreate(&e0));
+    LB_CHECK_CUDA(cudaEventCreate(&e1));
+    lb_status st = LB_OK;
+    for (int b = 0; b < LB_TILE_BUCKETS && st == LB_OK; ++b) {
+        // the bucket's largest size (the one that sets its cost), capped at nmax
+        const int n = std::min(16 * (b + 1), nmax);
+        if (b > 0 && n == std::min(16 * b, nmax)) {   // past nmax: the same size as the previous bucket
+            tiles_out[b] = tiles_out[b - 1];
+            if (us_out)
+                for (int t = 0; t < bt::NTILES; ++t) us_out[b * bt::NTILES + t] = us_out[(b - 1) * bt::NTILES + t];
+            continue;
+        }
+        // about 2e8 complex MACs per instance per timed launch, at least one jump term
+        const double macs = 2.0 * d * (double)n * n * n;
+        const int reps = (int)std::max(1.0, std::min(64.0, 2e8 / macs));
+        float best = 0.f;
+        int bi = 0;
+        for (int t = 0; t < bt::NTILES; ++t) {
+            bt::k_tune_jump<<<ninst, bt::BT, smem, s>>>(t, n, d, buf, 1);   // warm-up
+            lb_note_launch();
+            cudaEventRecord(e0, s);
+            bt::k_tune_jump<<<ninst, bt::BT, smem, s>>>(t, n, d, buf, reps);
+            lb_note_launch();
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) { st = LB_CUDA_ERROR; break; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            const float us = 1000.f * ms / reps;   // one jump term per instance, all instances side by side
+            if (us_out) us_out[b * bt::NTILES + t] = us;
+            if (t == 0 || us < best) { best = us; bi = t; }
+        }
+        tiles_out[b] = bi;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (cudaGetLastError() != cudaSuccess) return LB_CUDA_ERROR;
+    return st;
+}
 
 extern "C" size_t lindblad_batched_workspace_bytes(int count, const int* n, int d, const lb_opts* opts) {
     (void)opts;
@@ -1136,7 +1319,7 @@ extern "C" lb_status steady_state_batched(int count, const int* n, int d, const 
     if (opts) o = *opts;
     const int m = std::min(std::max(o.krylov_m, bt::PK + 2), bt::MB);
     bt::Plan p;
-    if (!bt::make_plan(count, n, d, p)) return LB_INVALID_ARG;
+    if (!bt::make_plan(count, n, d, p, o.batched_tiles)) return LB_INVALID_ARG;
     if (p.bytes > ws_bytes) return LB_WORKSPACE_TOO_SMALL;
     char* ws = static_cast<char*>(workspace);
     bt::Inst* d_inst = reinterpret_cast<bt::Inst*>(ws + p.off_inst);

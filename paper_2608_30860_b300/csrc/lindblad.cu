@@ -400,6 +400,7 @@ void lb_default_opts(lb_opts* o) {
     o->schur_tol = 1e-12;
     o->recycle_k = 8;
     o->gauge_c = nullptr;
+    o->batched_tiles = nullptr;
 }
 
 const char* lb_status_string(int st) {

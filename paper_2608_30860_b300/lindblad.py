@@ -8,7 +8,9 @@ lindbladian_apply, steady_state, low_spectrum, lindblad_destroy.
 from __future__ import annotations
 
 import ctypes
+import json
 import os
+import time
 from dataclasses import dataclass
 
 import torch
@@ -42,7 +44,7 @@ class LbOpts(ctypes.Structure):
                 ("gmres_m", ctypes.c_int), ("sylv_block", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("keep_ritz", ctypes.c_int), ("route", ctypes.c_int), ("eig_cond_max", ctypes.c_double),
                 ("schur_tol", ctypes.c_double), ("recycle_k", ctypes.c_int),
-                ("gauge_c", ctypes.POINTER(ctypes.c_double))]
+                ("gauge_c", ctypes.POINTER(ctypes.c_double)), ("batched_tiles", ctypes.POINTER(ctypes.c_int))]
 
 
 class LbInfo(ctypes.Structure):
@@ -98,6 +100,10 @@ def load_library(path: str = LIB_PATH):
     lib.steady_state_adjoint.restype = i
     lib.lindblad_batched_workspace_bytes.argtypes = [i, P(i), i, P(LbOpts)]
     lib.lindblad_batched_workspace_bytes.restype = sz
+    lib.lindblad_batched_tune_workspace_bytes.argtypes = [i, i]
+    lib.lindblad_batched_tune_workspace_bytes.restype = sz
+    lib.lindblad_batched_tune.argtypes = [i, i, vp, sz, P(i), P(ctypes.c_float), vp]
+    lib.lindblad_batched_tune.restype = i
     lib.steady_state_batched.argtypes = [i, P(i), i, vp, vp, vp, vp, sz, P(LbOpts), P(LbInfo), vp]
     lib.steady_state_batched.restype = i
     lib.lindbladian_apply_noalloc.argtypes = [vp, vp, i, i, vp, vp, vp]
@@ -353,12 +359,58 @@ def unpack_batch(rho: torch.Tensor, ns):
     return out
 
 
+LB_TILE_BUCKETS = 16
+LB_TILE_SHAPES = 4
+TILE_NAMES = ["32x32/k32/4x1", "64x32/k16/4x2", "64x64/k16/4x4", "32x64/k16/2x4"]
+
+
+def batched_tune(d: int, nmax: int = 160, cache: str | None = None, device=None) -> dict:
+    """Tile autotuner of the batched engine: times the complex64 jump term of every tile shape on one
+    synthetic instance per SM for each 16-wide size bucket (lindblad_batched_tune) and returns
+    {"tiles": [shape per bucket], "us": [[time per shape] per bucket], ...}.  With `cache` (a JSON path),
+    a stored result for the same device, d and nmax is reused and a new one is written there."""
+    dev = torch.device("cuda" if device is None else device)
+    key = {"device": torch.cuda.get_device_name(dev), "d": int(d), "nmax": int(nmax), "shapes": TILE_NAMES}
+    if cache and os.path.exists(cache):
+        with open(cache) as f:
+            got = json.load(f)
+        if all(got.get(k) == v for k, v in key.items()):
+            got["cached"] = True
+            return got
+    lib = load_library()
+    nbytes = lib.lindblad_batched_tune_workspace_bytes(int(d), int(nmax))
+    if nbytes == 0:
+        raise LindbladError(-1, "lindblad_batched_tune_workspace_bytes")
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    tiles = (ctypes.c_int * LB_TILE_BUCKETS)()
+    us = (ctypes.c_float * (LB_TILE_BUCKETS * LB_TILE_SHAPES))()
+    t0 = time.perf_counter()
+    st = lib.lindblad_batched_tune(int(d), int(nmax), ws.data_ptr(), nbytes, tiles, us, _stream())
+    if st != 0:
+        raise LindbladError(st, "lindblad_batched_tune")
+    out = dict(key, tiles=list(tiles), tune_s=time.perf_counter() - t0, cached=False,
+               buckets=[f"n<={16 * (b + 1)}" for b in range(LB_TILE_BUCKETS)],
+               us=[[float(us[b * LB_TILE_SHAPES + t]) for t in range(LB_TILE_SHAPES)] for b in range(LB_TILE_BUCKETS)])
+    if cache:
+        os.makedirs(os.path.dirname(os.path.abspath(cache)), exist_ok=True)
+        with open(cache, "w") as f:
+            json.dump(out, f, indent=1)
+    return out
+
+
 def steady_state_batched(ns, d: int, H: torch.Tensor, L: torch.Tensor, opts: LbOpts | None = None,
-                         rho: torch.Tensor | None = None, workspace: torch.Tensor | None = None):
-    """Steady states of len(ns) Lindbladians packed by pack_batch (device complex128).
+                         rho: torch.Tensor | None = None, workspace: torch.Tensor | None = None, tiles=None):
+    """Steady states of len(ns) Lindbladians packed by pack_batch (device complex128).  tiles: the
+    autotuner's tile shape per size bucket (batched_tune(...)["tiles"]); None = shape 0 everywhere.
     Returns (rho packed, list of info dicts, status); raises on a negative status."""
     lib = load_library()
     o = opts or default_opts(krylov_m=32)
+    if tiles is not None:
+        if len(tiles) != LB_TILE_BUCKETS or not all(0 <= int(t) < LB_TILE_SHAPES for t in tiles):
+            raise ValueError("tiles: one shape in [0, LB_TILE_SHAPES) per size bucket")
+        table = (ctypes.c_int * LB_TILE_BUCKETS)(*[int(t) for t in tiles])
+        o = LbOpts.from_buffer_copy(o)
+        o.batched_tiles = ctypes.cast(table, ctypes.POINTER(ctypes.c_int))
     count = len(ns)
     total = sum(int(v) * int(v) for v in ns)
     if H.numel() != total or L.numel() != d * total:

@@ -44,8 +44,8 @@ def test_opts_struct_layout_and_defaults(lib):
     o = B.default_opts()
     assert o.tol == 1e-10 and o.krylov_m == 20 and o.gmres_m == 40 and o.eta == 1.0 and o.precision == B.LB_PREC_FP64
     assert o.route == B.LB_ROUTE_SCHUR and o.eig_cond_max == 1e3
-    assert o.schur_tol == 1e-12 and o.recycle_k == 8 and not o.gauge_c
-    assert ctypes.sizeof(B.LbOpts) == 96   # C layout: 5 doubles, 9 ints, a pointer, natural padding
+    assert o.schur_tol == 1e-12 and o.recycle_k == 8 and not o.gauge_c and not o.batched_tiles
+    assert ctypes.sizeof(B.LbOpts) == 104  # C layout: 5 doubles, 9 ints, two pointers, natural padding
     assert ctypes.sizeof(B.LbInfo) == 96
 
 

@@ -37,11 +37,11 @@ def _kerr(p):
     return gi.kerr_cat(p["n"], K=p["K"], eps2=p["eps2"], kappa2=p["kappa2"], kappa1=p["kappa1"])
 
 
-def _run(B, systems, opts=None):
+def _run(B, systems, opts=None, tiles=None):
     ns = [H.shape[0] for H, _ in systems]
     d = len(systems[0][1])
     Hp, Lp = B.pack_batch([_cuda(H) for H, _ in systems], [_cuda(np.stack(Ls)) for _, Ls in systems])
-    rho, infos, st = B.steady_state_batched(ns, d, Hp, Lp, opts=opts)
+    rho, infos, st = B.steady_state_batched(ns, d, Hp, Lp, opts=opts, tiles=tiles)
     torch.cuda.synchronize()
     return B.unpack_batch(rho, ns), infos, st
 
@@ -205,3 +205,33 @@ def test_batched_tight_tolerance_parity_at_mixed_bar(B):
         err = np.linalg.norm(ge - re_) / np.linalg.norm(re_)
         print(f"n={H.shape[0]} even-sector err {err:.2e}")
         assert err < 1e-9
+
+
+def test_tile_autotuner_and_every_tile_shape(B, tmp_path):
+    """The autotuner times every shape for every size bucket and caches its choice; the batched solve gives
+    the same converged states with each of the four tile shapes forced and with the tuned table (the
+    shapes change only the blocking and summation order of the complex64 jump term)."""
+    cache = str(tmp_path / "tiles.json")
+    tune = B.batched_tune(2, nmax=100, cache=cache)
+    assert not tune["cached"] and len(tune["tiles"]) == B.LB_TILE_BUCKETS
+    assert all(0 <= t < B.LB_TILE_SHAPES for t in tune["tiles"])
+    assert all(all(u > 0 for u in row) for row in tune["us"])
+    print("tiles", [B.TILE_NAMES[t] for t in tune["tiles"][:7]], "us", tune["us"][:7])
+    again = B.batched_tune(2, nmax=100, cache=cache)
+    assert again["cached"] and again["tiles"] == tune["tiles"]
+    params = gi.kerr_cat_sweep(6, seed=5, nmin=17, nmax=100)
+    systems = [_kerr(p) for p in params]
+    ref = None
+    for tiles in ([0] * 16, [1] * 16, [2] * 16, [3] * 16, tune["tiles"]):
+        rhos, infos, st = _run(B, systems, tiles=tiles)
+        assert st == 0, [i["status"] for i in infos]
+        for (H, Ls), rho, info in zip(systems, rhos, infos):
+            assert info["residual_max"] < TOL
+            assert _residual_max(H, Ls, rho) < TOL
+        even = [_parity_even(r.cpu().numpy()) for r in rhos]
+        if ref is None:
+            ref = even
+        for a, b in zip(even, ref):
+            assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-7
+    with pytest.raises(ValueError):
+        B.steady_state_batched([4], 2, _cuda(np.zeros(16, complex)), _cuda(np.zeros(32, complex)), tiles=[7] * 16)
