@@ -154,10 +154,14 @@ def cpu_baseline(n_sites=12, d_sample=1, repeats=1):
             "extrapolation": {"jump_factor": k_scale, "sylvester_factor": s_scale}}
 
 
-# DRAM bytes (read + write) per jump-term k_tc_gemm launch, recorded from an ncu capture of the kernel
-# revision named below (None until the current revision has been captured)
-JUMP_GEMM_TRAFFIC_BYTES = None
-JUMP_GEMM_TRAFFIC_NOTE = "recorded profile value of the named kernel revision, not measured in this run"
+# DRAM bytes (read + write) per jump-term k_tc_gemm launch at n = 4096, d = 12: the two jump-term launches
+# of one application captured on the 10-site chain (n = 1024, d = 10; dram__bytes_read.sum +
+# dram__bytes_write.sum, profiles/tc_gemm_jump_tfim10_n1024.md): product (1) 99.6 + 53.4 MB, product (2)
+# 177.3 + 0.06 MB, mean 165.2 MB per launch; the operand planes scale as d n^2, so x (12/10) x 16 = 19.2
+# gives 3.17 GB per launch (the algorithmic bytes are 3.29 GB: L2 absorbs part of product (1)'s writes)
+JUMP_GEMM_TRAFFIC_BYTES = 3.17e9
+JUMP_GEMM_TRAFFIC_NOTE = ("ncu DRAM bytes of the current k_tc_gemm revision at n = 1024, d = 10, scaled by d n^2 to "
+                          "n = 4096, d = 12 (the full-size capture needs more than one pass)")
 
 SWEEP = dict(workload="kerr_cat_sweep_1024", count=1024, seed=0, n_range=[16, 160], d=2,
              eps2=[1.0, 8.0], K=[0.5, 2.0], kappa1=[1e-3, 1e-1], kappa2=1.0)
