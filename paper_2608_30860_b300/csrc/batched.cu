@@ -136,7 +136,7 @@ __device__ void cta_gemm(const C* A, int opA, const C* B, int opB, C* Cm, int n,
 // tc + j TN/RN: consecutive lanes read consecutive shared-memory columns).  sa: TM x (KT+1), sb: KT x (TN+1)
 // complex64 tiles.  The tile shape is the autotuner's choice per instance size.
 template <int TM, int TN, int KT, int RM, int RN>
-__device__ __noinline__ void tgemm_c64(const float2* __restrict__ A, long long a_seg, const float2* __restrict__ B,
+__device__ __forceinline__ void tgemm_c64(const float2* __restrict__ A, long long a_seg, const float2* __restrict__ B,
                                        long long b_seg, int opB, int nseg, float2* __restrict__ Cm, int M, int N, int K,
                                        float alpha, float2* sa, float2* sb) {
     constexpr int RG = TM / RM, CG = TN / RN;
@@ -203,9 +203,6 @@ __device__ __noinline__ void tgemm_c64(const float2* __restrict__ A, long long a
 
 // the tile shapes the autotuner chooses from: (TM, TN, KT, RM, RN)
 constexpr int NTILES = 4;
-__host__ __device__ inline const char* tile_name(int t) {
-    return t == 0 ? "32x32/k32/4x1" : t == 1 ? "64x32/k16/4x2" : t == 2 ? "64x64/k16/4x4" : "32x64/k16/2x4";
-}
 __device__ inline void tgemm_dispatch(int tile, const float2* A, long long a_seg, const float2* B, long long b_seg,
                                       int opB, int nseg, float2* Cm, int M, int N, int K, float alpha, float2* sa,
                                       float2* sb) {
@@ -679,6 +676,16 @@ __device__ void jump32(const View& v, const float2* Zin, float2* y, float alpha,
     const long long nn = (long long)v.n * v.n;
     float2* sa = reinterpret_cast<float2*>(sm.ga);
     float2* sb = reinterpret_cast<float2*>(sm.gb);
+    if (v.tile == 0) {
+        // shape 0: the general CTA GEMM, one product per jump (P_j = L~_j Z, then y += alpha P_j L~_j^dag)
+        for (int j = 0; j < v.d; ++j)
+            cta_gemm(v.Ltf + j * nn, 0, Zin, 0, v.Pf + j * nn, v.n, make_float2(1.f, 0.f), make_float2(0.f, 0.f), 0,
+                     sa, sb);
+        for (int j = 0; j < v.d; ++j)
+            cta_gemm(v.Pf + j * nn, 0, v.Ltf + j * nn, 2, y, v.n, make_float2(alpha, 0.f), make_float2(1.f, 0.f),
+                     j > 0, sa, sb);
+        return;
+    }
     // (1) [P_1; ..; P_d] = [L~_1; ..; L~_d] Z  (one stacked product, M = d n)
     tgemm_dispatch(v.tile, v.Ltf, 0, Zin, 0, 0, 1, v.Pf, v.d * v.n, v.n, v.n, 1.f, sa, sb);
     // (2) y = alpha sum_j P_j L~_j^dag  (the sum over j inside one accumulation)
@@ -1229,6 +1236,14 @@ __global__ void __launch_bounds__(BT, 1) k_tune_jump(int tile, int n, int d, flo
     float2* sa = reinterpret_cast<float2*>(sm.ga);
     float2* sb = reinterpret_cast<float2*>(sm.gb);
     for (int r = 0; r < reps; ++r) {
+        if (tile == 0) {
+            for (int j = 0; j < d; ++j)
+                cta_gemm(L + j * nn, 0, Z, 0, P + j * nn, n, make_float2(1.f, 0.f), make_float2(0.f, 0.f), 0, sa, sb);
+            for (int j = 0; j < d; ++j)
+                cta_gemm(P + j * nn, 0, L + j * nn, 2, y, n, make_float2(-1.f, 0.f), make_float2(1.f, 0.f), j > 0, sa,
+                         sb);
+            continue;
+        }
         tgemm_dispatch(tile, L, 0, Z, 0, 0, 1, P, d * n, n, n, 1.f, sa, sb);
         tgemm_dispatch(tile, P, nn, L, nn, 2, d, y, n, n, n, -1.f, sa, sb);
     }

@@ -361,7 +361,7 @@ def unpack_batch(rho: torch.Tensor, ns):
 
 LB_TILE_BUCKETS = 16
 LB_TILE_SHAPES = 4
-TILE_NAMES = ["32x32/k32/4x1", "64x32/k16/4x2", "64x64/k16/4x4", "32x64/k16/2x4"]
+TILE_NAMES = ["32x32/k32/4x1/per-jump", "64x32/k16/4x2", "64x64/k16/4x4", "32x64/k16/2x4"]
 
 
 def batched_tune(d: int, nmax: int = 160, cache: str | None = None, device=None) -> dict:
