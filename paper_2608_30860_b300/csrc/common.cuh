@@ -53,11 +53,12 @@ struct ZGemmArgs {
     int batch;    // number of (A_b, B_b) pairs
     int reduce;   // 1: C = alpha * sum_b op(A_b) op(B_b) + beta C ; 0: C_b = alpha op(A_b) op(B_b) + beta C_b
     int herm;     // 1 (reduce = 1, M = N): the result is Hermitian (alpha, beta real, C Hermitian on entry):
-                  // only the tiles on and above the diagonal are computed, the rest is mirrored
+                  // only the tiles on and above the diagonal are computed, the rest is mirrored; 2: the same
+                  // and the diagonal's imaginary part is set to zero (an exactly Hermitian result)
 };
 
-// C[i][j] = conj(C[j][i]) for i > j and Im C[i][i] = 0 (n x n, leading dimension ld)
-int mat_mirror_lower(cplx* C, int n, long long ld, cudaStream_t s);
+// C[i][j] = conj(C[j][i]) for i > j, and Im C[i][i] = 0 when real_diag (n x n, leading dimension ld)
+int mat_mirror_lower(cplx* C, int n, long long ld, cudaStream_t s, int real_diag = 0);
 
 // host launchers (defined in the .cu files)
 int zgemm_f64(const ZGemmArgs& a, cudaStream_t s);

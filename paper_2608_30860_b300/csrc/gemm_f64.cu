@@ -91,9 +91,11 @@ __global__ void __launch_bounds__(256) zgemm_f64_kernel(ZGemmArgs a) {
     }
 }
 
-// C[i][j] = conj(C[j][i]) below the diagonal and Im C[i][i] = 0 (the result is Hermitian), 32 x 32 tiles
-// through shared memory (coalesced both ways)
-__global__ void k_mirror_lower(cplx* C, int n, long long ld) {
+// C[i][j] = conj(C[j][i]) below the diagonal, 32 x 32 tiles through shared memory (coalesced both ways);
+// real_diag: also Im C[i][i] = 0, so that the result is exactly Hermitian.  (The Krylov solvers keep the
+// computed diagonal: zeroing its rounding-level imaginary part inside the Phi-Arnoldi operator stalled the
+// FP64 steady state of slowly mixing Kerr cats at ~1e-6.)
+__global__ void k_mirror_lower(cplx* C, int n, long long ld, int real_diag) {
     __shared__ cplx t[32][33];
     const int bi = blockIdx.y, bj = blockIdx.x;   // destination tile (bi, bj), bi >= bj
     if (bi < bj) return;
@@ -106,15 +108,15 @@ __global__ void k_mirror_lower(cplx* C, int n, long long ld) {
     for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
         const int r = bi * 32 + yy, c = bj * 32 + tx;
         if (r < n && c < n && r > c) C[(long long)r * ld + c] = cconj(t[tx][yy]);
-        if (r < n && r == c) C[(long long)r * ld + c].y = 0.0;   // a Hermitian diagonal is real
+        if (real_diag && r < n && r == c) C[(long long)r * ld + c].y = 0.0;   // a Hermitian diagonal is real
     }
 }
 
 }  // namespace
 
-int mat_mirror_lower(cplx* C, int n, long long ld, cudaStream_t s) {
+int mat_mirror_lower(cplx* C, int n, long long ld, cudaStream_t s, int real_diag) {
     const int nt = (n + 31) / 32;
-    k_mirror_lower<<<dim3(nt, nt), dim3(32, 8), 0, s>>>(C, n, ld); lb_note_launch();
+    k_mirror_lower<<<dim3(nt, nt), dim3(32, 8), 0, s>>>(C, n, ld, real_diag); lb_note_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -124,5 +126,5 @@ int zgemm_f64(const ZGemmArgs& a, cudaStream_t s) {
     dim3 grid((a.N + BN - 1) / BN, (a.M + BM - 1) / BM, a.reduce ? 1 : a.batch);
     zgemm_f64_kernel<<<grid, 256, 0, s>>>(a); lb_note_launch();
     if (cudaGetLastError() != cudaSuccess) return -1;
-    return a.herm ? mat_mirror_lower(a.C, a.M, a.ldc, s) : 0;
+    return a.herm ? mat_mirror_lower(a.C, a.M, a.ldc, s, a.herm == 2) : 0;
 }

@@ -680,7 +680,7 @@ lb_status phi_apply(lindblad_handle h, const void* X_dev, void* Y_dev, int flags
     if (h->case1) return LB_S_SINGULAR;
     cudaStream_t s = (cudaStream_t)stream;
     const int form = flags & LB_APPLY_FORM_M ? 1 : 0;
-    const int herm = flags & LB_APPLY_HERMITIAN ? 1 : 0;
+    const int herm = flags & LB_APPLY_HERMITIAN ? 2 : 0;   // 2: an exactly Hermitian result (real diagonal)
     const cplx* X = (const cplx*)X_dev;
     cplx* Y = (cplx*)Y_dev;
     if (precision == LB_PREC_MIXED && !h->mixed_ready) return LB_NOT_IMPLEMENTED;
@@ -700,7 +700,7 @@ lb_status jump_apply(lindblad_handle h, const void* X_dev, void* Y_dev, int flag
     cudaStream_t s = (cudaStream_t)stream;
     const cplx* X = (const cplx*)X_dev;
     cplx* Y = (cplx*)Y_dev;
-    const int herm = flags & LB_APPLY_HERMITIAN ? 1 : 0;
+    const int herm = flags & LB_APPLY_HERMITIAN ? 2 : 0;   // 2: an exactly Hermitian result (real diagonal)
     if (!(flags & LB_APPLY_SCHUR)) {
         // original basis: L_j themselves (FP64), or via Schur coordinates on the tensor cores
         if (precision != LB_PREC_MIXED)

@@ -144,7 +144,7 @@ int jump_mixed(lb_handle_s* h, cudaStream_t s, const cplx* Z, cplx* Y, double al
     prof_begin(h, s, 0);
     if (p2.ksplit > 1 && cudaMemsetAsync(Y, 0, (size_t)n * n * sizeof(cplx), s) != cudaSuccess) return -1;
     int r = tc_gemm_launch(m->maps, p2, (n + tc::BM - 1) / tc::BM, (n + tc::BN - 1) / tc::BN, s);
-    if (!r && herm) r = mat_mirror_lower(Y, n, n, s);
+    if (!r && herm) r = mat_mirror_lower(Y, n, n, s, herm == 2);
     // algorithmic work: the full product, or its Hermitian half (n (n + 1) / 2 entries)
     prof_end(h, s, 0, (herm ? 4.0 * (n + 1) : 8.0 * n) * d * (double)n * n);
     return r;
