@@ -750,8 +750,6 @@ static lb_status steady_state_body(lindblad_handle h, void* rho_dev, const lb_op
     if (o.precision == LB_PREC_MIXED && !h->mixed_ready) return LB_NOT_IMPLEMENTED;
     cudaStream_t s = (cudaStream_t)stream;
     const double t0 = now_ms();
-    const int n = h->n;
-    const long long nn = (long long)n * n;
     lb_info inf{};
     inf.schur_backward_err = h->schur_err;
     inf.min_abs_re_T = h->min_re_T;
