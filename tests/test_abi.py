@@ -77,3 +77,20 @@ def test_batched_workspace_query_host_logic():
     assert B.lindblad_batched_workspace_bytes([1], 2) == 0
     lib = B.load_library()
     assert lib.lindblad_batched_workspace_bytes(0, (ctypes.c_int * 1)(16), 2, None) == 0
+
+
+def test_tuner_and_test_hook_arguments_rejected_on_host():
+    """Argument checks that return before any CUDA call: the batched tile autotuner's workspace query and
+    entry point, and the bounded-wait test hook."""
+    import paper_2608_30860_b300 as B
+    lib = B.load_library()
+    assert lib.lindblad_batched_tune_workspace_bytes(0, 100) == 0      # d < 1
+    assert lib.lindblad_batched_tune_workspace_bytes(2, 1) == 0        # nmax < 2
+    assert lib.lindblad_batched_tune_workspace_bytes(2, 300) == 0      # nmax > 256
+    tiles = (ctypes.c_int * B.LB_TILE_BUCKETS)()
+    assert lib.lindblad_batched_tune(0, 100, None, 0, tiles, None, None) == -1
+    assert lib.lindblad_batched_tune(2, 100, None, 0, tiles, None, None) == -1   # null workspace
+    assert lib.lb_test_bounded_wait(None, 0, 10.0) == -1
+    assert B.LB_TILE_BUCKETS == 16 and B.LB_TILE_SHAPES == len(B.TILE_NAMES) == 4
+    src = open(HEADER).read()
+    assert "#define LB_TILE_BUCKETS 16" in src and "#define LB_TILE_SHAPES 4" in src
