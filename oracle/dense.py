@@ -82,7 +82,8 @@ def resolvent_S(G, lam):
 
 
 def deflation_term(n):
-    """Matrix of rho -> Tr(rho) I, i.e. |I><I| in column-major vec."""
+    """Matrix of rho -> Tr(rho) I, i.e. |I><I| in column-major vec: the deflation term of
+    Eq. steady_state_linear_problem."""
     v = vec(np.eye(n, dtype=np.complex128))
     return np.outer(v, v)
 
@@ -146,6 +147,7 @@ def G_rows(H, Ls, idx):
 
 # ----------------------------------------------------------------------------- steady state
 def hermitize_normalize(rho):
+    """(rho + rho^dag) / 2 divided by its trace: the reconstruction step of Alg. 4."""
     r = 0.5 * (rho + dag(rho))
     return r / np.trace(r).real
 
@@ -160,7 +162,8 @@ def steady_state_lu(H, Ls, eta=1.0):
 
 
 def steady_state_svd(H, Ls):
-    """rho_inf as the right singular vector of L for its smallest singular value."""
+    """rho_inf as the right singular vector of L for its smallest singular value (the null vector of the
+    Lindbladian of Eq. lindblad_def; cross-check of the deflated solve)."""
     n = H.shape[0]
     _, s, Vh = np.linalg.svd(liouvillian(H, Ls))
     x = Vh[-1].conj()
@@ -169,6 +172,7 @@ def steady_state_svd(H, Ls):
 
 # ----------------------------------------------------------------------------- spectra
 def liouvillian_eigenvalues(H, Ls):
+    """All eigenvalues of the dense Lindbladian of Eq. lindblad_def."""
     return sla.eigvals(liouvillian(H, Ls))
 
 
@@ -186,7 +190,8 @@ def low_spectrum(H, Ls, k, zero_tol=None):
 
 
 def low_spectrum_with_vectors(H, Ls, k):
-    """k smallest-|lambda| nonzero eigenpairs (values, list of n x n eigenvectors)."""
+    """k smallest-|lambda| nonzero eigenpairs (values, list of n x n eigenvectors): the low-lying spectrum
+    of Sec. 4.2 by dense eigendecomposition."""
     n = H.shape[0]
     ev, V = sla.eig(liouvillian(H, Ls))
     order = np.argsort(np.abs(ev))[1:k + 1]
@@ -249,7 +254,8 @@ def steady_state_gradient(H_of_theta, Ls_of_theta, dL_super_of_theta, theta, O, 
 
 # ----------------------------------------------------------------------------- misc
 def choi(superop, n):
-    """Choi matrix sum_ij |i><j| (x) E(|i><j|) of a superoperator given as a dense matrix."""
+    """Choi matrix sum_ij |i><j| (x) E(|i><j|) of a superoperator given as a dense matrix (its positive
+    semidefiniteness is the complete positivity of Theorem 1)."""
     C = np.zeros((n * n, n * n), dtype=np.complex128)
     for i in range(n):
         for j in range(n):
@@ -261,7 +267,8 @@ def choi(superop, n):
 
 
 def superop_adjoint_apply(superop, X, n):
-    """E^*(X) for the Hilbert-Schmidt inner product: the conjugate-transpose matrix."""
+    """E^*(X) for the Hilbert-Schmidt inner product (the superoperator adjoint of Sec. 1.2's notation):
+    the conjugate-transpose matrix."""
     return unvec(dag(superop) @ vec(X), n)
 
 

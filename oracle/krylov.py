@@ -84,14 +84,14 @@ class System:
 
     # -- superoperators ---------------------------------------------------------
     def K(self, X):
-        """Jump part K(X) = sum_j L_j X L_j^dag."""
+        """Jump part K(X) = sum_j L_j X L_j^dag (Eq. lindblad_decomposition)."""
         out = np.zeros_like(X)
         for L in self.Ls:
             out += L @ X @ dag(L)
         return out
 
     def S(self, X):
-        """No-jump part S(X) = G X + X G^dag."""
+        """No-jump part S(X) = G X + X G^dag (Eq. lindblad_decomposition, G of Eq. G)."""
         return self.G @ X + X @ dag(self.G)
 
     def L(self, X):
@@ -99,7 +99,8 @@ class System:
         return self.S(X) + self.K(X)
 
     def L_adjoint(self, X):
-        """L^*(X) = G^dag X + X G + sum_j L_j^dag X L_j (Hilbert-Schmidt adjoint)."""
+        """L^*(X) = G^dag X + X G + sum_j L_j^dag X L_j (Hilbert-Schmidt adjoint; the adjoint system of the
+        Remark on differentiating the steady state, Sec. 4.1)."""
         out = dag(self.G) @ X + X @ self.G
         for L in self.Ls:
             out += dag(L) @ X @ L
@@ -155,7 +156,8 @@ class System:
         return Z + (c * np.trace(Z) / denom) * W
 
     def shifted_deflated(self, X, mu, eta):
-        """(mu - L~_eta)(X) = mu X - L(X) - eta Tr(X) I."""
+        """(mu - L~_eta)(X) = mu X - L(X) - eta Tr(X) I: the deflated operator of
+        Eq. steady_state_linear_problem, shifted as in Alg. 5."""
         return mu * X - self.L(X) - eta * np.trace(X) * np.eye(self.n)
 
 
