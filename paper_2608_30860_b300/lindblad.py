@@ -372,9 +372,14 @@ def batched_tune(d: int, nmax: int = 160, cache: str | None = None, device=None)
     dev = torch.device("cuda" if device is None else device)
     key = {"device": torch.cuda.get_device_name(dev), "d": int(d), "nmax": int(nmax), "shapes": TILE_NAMES}
     if cache and os.path.exists(cache):
-        with open(cache) as f:
-            got = json.load(f)
-        if all(got.get(k) == v for k, v in key.items()):
+        try:
+            with open(cache) as f:
+                got = json.load(f)
+        except (OSError, ValueError):
+            got = {}   # unreadable cache: tune again and overwrite it
+        if isinstance(got, dict) and all(got.get(k) == v for k, v in key.items()) and \
+                len(got.get("tiles", [])) == LB_TILE_BUCKETS and \
+                all(isinstance(t, int) and 0 <= t < LB_TILE_SHAPES for t in got["tiles"]):
             got["cached"] = True
             return got
     lib = load_library()
