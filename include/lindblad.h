@@ -237,8 +237,12 @@ lb_status implicit_euler(lindblad_handle h, const void* rho0_dev, double dt, int
 
 /* The k smallest-|lambda| nonzero eigenvalues of L by shift-invert Arnoldi on
  * (mu - L~_eta)^{-1} (Alg. 5), each application a GMRES solve right-preconditioned by
- * Precond(., mu, eta) (Alg. 2), recycled across cycles and across applications (App. A.2).  Thick (Krylov-Schur) restarts keep opts->keep_ritz pairs;
- * stop when max_k ||L v_k - lambda_k v_k||_max / ||v_k||_max < opts->tol.
+ * Precond(., mu, eta) (Alg. 2), recycled across cycles and across applications (App. A.2); every inner
+ * solve's true residual is checked with one explicit application of (mu - L~_eta), and a recycled pair
+ * that disagrees with it is dropped.  Thick (Krylov-Schur) restarts keep opts->keep_ritz pairs;
+ * stop when max_k ||L v_k - lambda_k v_k||_max / ||v_k||_max < opts->tol.  With LB_PREC_MIXED the inner
+ * solves run on the tensor cores while the eigen-residual falls (to 1e-6 or until it stops halving),
+ * then the outer iteration restarts explicitly in FP64 from the sum of the k wanted Schur vectors.
  *   evals_host : k complex128 (host memory), sorted by |lambda|, then Re descending.
  *   evecs_dev  : nullable; k stacked n x n device eigenvectors (raw, traceless).
  * Errors: LB_INVALID_ARG (k < 1 or k > m - 2), LB_ETA_EXCLUDED, LB_S_SINGULAR (mu = 0 with

@@ -427,7 +427,7 @@ static lb_status low_spectrum_body(lindblad_handle h, int k, double mu, double e
     int j0 = 0, restart = 0;
     double worst = INFINITY;
     // mixed precision: the inner solves run on the tensor cores while the eigen-residual falls, then in
-    // FP64 (W recomputed in FP64), keeping the thick-restart basis: the FP64 cycles refine the pairs
+    // FP64 (W recomputed in FP64) after an explicit restart from the wanted Schur vectors
     int prec = o.precision;
     double prev_worst = INFINITY;
     const bool verbose = std::getenv("LB_VERBOSE") != nullptr;   // diagnostics on stderr, no effect on results
